@@ -1,0 +1,189 @@
+/*
+ * fde.h - C ABI of the GB300 (sm_103a) ADMM / Toeplitz-FFT library.
+ *
+ * The library solves the box-constrained convex quadratic program of
+ * Pougkakiotis, Pearson, Leveque, Gondzio, "Fast Solution Methods for Convex
+ * Fractional Differential Equation Optimization" (arXiv:1907.13428):
+ *
+ *   min 1/2 (y - ybar)^T J1 (y - ybar) + 1/2 u^T J2 u
+ *   s.t. B y + psi u = psi g,  ya <= y <= yb,  ua <= u <= ub          (Sec. 4, Eq. FDEOpt)
+ *
+ * with B = psi (C_t (x) I - I (x) (X (x) I + I (x) Y)) the psi-scaled three-level
+ * Toeplitz operator of Eq. (FDE constraint matrix) and Section 5, where
+ * X = d+ L_x + d- L_x^T and Y = e+ L_y + e- L_y^T are built from shifted
+ * Gruenwald-Letnikov matrices (Eq. RL_GL), C_t is the Gruenwald-Letnikov time
+ * matrix (Eq. Caputo matrix; alpha_t = 1 is implicit Euler) and J1 = diag(w),
+ * J2 = gamma diag(w) (Eq. discretized Objective function).
+ *
+ * Conventions shared by every entry point:
+ *  - Vectors have N = nt*nx*ny entries laid out [t][x1][x2] (x2 fastest; the
+ *    lexicographic ordering of Section 2), interior points only, times
+ *    t_1..t_nt (t = 0 is the zero initial state).
+ *  - Unless stated otherwise, array arguments are DEVICE pointers owned by
+ *    the caller, contiguous, of element type double (FDE_FP64 / FDE_MIXED) or
+ *    float (FDE_FP32). They must stay valid until the work queued on `stream`
+ *    has finished.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). All GPU work is queued on it; calls return when the work is
+ *    queued, except where a call must read a convergence scalar back (PCG,
+ *    ADMM), which synchronises `stream`.
+ *  - The library owns its workspace: fde_setup allocates it (cudaMalloc),
+ *    fde_destroy frees it. A problem handle must not be used by two host
+ *    threads at once, nor on two streams concurrently.
+ *  - Every int-returning call returns FDE_OK (0) or a negative FDE_E* code;
+ *    nothing throws across the ABI. fde_strerror gives a static message.
+ *    On error, outputs are unspecified except where stated.
+ */
+#ifndef FDE_H
+#define FDE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum fde_status {
+  FDE_OK = 0,
+  FDE_EINVAL = -1,       /* argument outside its domain                                   */
+  FDE_ENOMEM = -2,       /* device allocation failed                                      */
+  FDE_ECUDA = -3,        /* a CUDA call failed (see fde_last_cuda_error)                   */
+  FDE_ENOCONV = -4,      /* iteration cap reached; outputs hold the last iterate           */
+  FDE_EBREAKDOWN = -5,   /* PCG breakdown (p^T S p <= 0)                                   */
+  FDE_ENONFINITE = -6,   /* NaN or Inf met in a reduction                                  */
+  FDE_EUNSUPPORTED = -8  /* size or mode this build does not handle                       */
+};
+
+/* Arithmetic of an operator application or of a solve. */
+enum fde_precision {
+  FDE_FP64 = 0,   /* everything in double                                                   */
+  FDE_FP32 = 1,   /* operator/preconditioner in float, float arrays (fde_matvec/fde_precond) */
+  FDE_MIXED = 2   /* solves only: float operator+preconditioner inside a double-precision
+                     iterative-refinement loop; double arrays at the interface               */
+};
+
+enum fde_op {
+  FDE_OP_B = 0,   /* y = B x                                                                */
+  FDE_OP_BT = 1,  /* y = B^T x (left and right GL matrices swapped, time reversed)          */
+  FDE_OP_S = 2    /* y = S x = M1 x + B^T M2^-1 B x (Eq. generic ADMM normal equations)      */
+};
+
+/* Problem description (Sections 4 and 6.1). */
+typedef struct fde_params {
+  int nx, ny, nt;            /* interior points along x1, x2 and time steps; each in [1, 4096]  */
+  double T;                  /* final time (h_t = T/nt when time_step_mode == 0)                 */
+  double beta_x, beta_y;     /* spatial orders, each in (1, 2)                                   */
+  double alpha_t;            /* time order in (0, 1]; 1 = implicit Euler                         */
+  double dp, dm;             /* coefficients of L_x and L_x^T (x1 axis), >= 0                     */
+  double ep, em;             /* coefficients of L_y and L_y^T (x2 axis), >= 0                     */
+  double gamma;              /* control regularisation, > 0                                      */
+  int weights;               /* 0: trapezoid in time (last slice weight 1/2), 1: uniform         */
+  int time_step_mode;        /* 0: h_t = T/nt, 1: h_t = h_x = 1/(nx+1) (Section 6.1)             */
+} fde_params;
+
+/* ADMM options (Algorithm 1, Section 6.1). */
+typedef struct fde_admm_opts {
+  double delta;              /* penalty parameter: the penalty term is 1/(2 delta), > 0          */
+  double rho;                /* dual step length in (0, (1+sqrt 5)/2)                            */
+  double tol_admm;           /* infinity-norm tolerance on the three residuals of Section 6.1    */
+  int max_admm;              /* iteration cap                                                     */
+  int fixed_iters;           /* 1: run exactly max_admm iterations (no residual test)             */
+  int max_pcg;               /* PCG iteration cap per sub-problem (per refinement step in MIXED)  */
+  int inner_tol_mode;        /* 0: Section 6.1 rule 0.05 max{min residuals, tol_admm}; 1: fixed   */
+  double inner_tol;          /* relative residual target of each sub-solve when inner_tol_mode=1  */
+  int precision;             /* FDE_FP64 or FDE_MIXED                                            */
+  double inner_tol_mixed;    /* MIXED: relative residual target of the float PCG per refinement   */
+  int max_refine;            /* MIXED: cap on refinement steps per sub-problem                    */
+} fde_admm_opts;
+
+typedef struct fde_admm_stats {
+  int admm_iters;            /* iterations performed                                             */
+  int pcg_iters;             /* PCG iterations summed over all sub-problems                      */
+  int refine_steps;          /* MIXED: refinement corrections summed over sub-problems           */
+  int fp64_matvecs;          /* double-precision B or B^T applications                           */
+  double res_eq;             /* ||B y + psi (u - g)||_inf at exit                                */
+  double res_y;              /* ||y - z_y||_inf at exit                                          */
+  double res_u;              /* ||u - z_u||_inf at exit                                          */
+  double objective;          /* 1/2 (y-ybar)^T J1 (y-ybar) + 1/2 u^T J2 u at exit                */
+  double max_sub_relres;     /* largest final relative residual ||b - S y||/||b|| of a sub-solve */
+} fde_admm_stats;
+
+typedef struct fde_problem fde_problem;
+
+/* Create a problem: validate params, allocate the workspace and run the set-up
+ * kernels (Gruenwald-Letnikov weights of Eq. C_GL, circulant-embedding symbols
+ * of the Toeplitz factors, T. Chan circulants of Eq. (level 1 circulant
+ * optimization problem) and their DFTs; Section 5). `*out` receives the handle.
+ * Errors: FDE_EINVAL (orders outside their intervals, n < 1, gamma <= 0,
+ * negative coefficients), FDE_EUNSUPPORTED (an axis above 4096), FDE_ENOMEM,
+ * FDE_ECUDA. Synchronises `stream` before returning. */
+int fde_setup(const fde_params* params, fde_problem** out, void* stream);
+
+/* Release a problem and its workspace (NULL is allowed). */
+void fde_destroy(fde_problem* prob);
+
+/* Number of vector entries N = nt*nx*ny (0 for NULL). */
+long long fde_size(const fde_problem* prob);
+
+/* psi = min{h_t^alpha_t, h_x^beta_x, h_y^beta_y} (Section 5). */
+double fde_psi(const fde_problem* prob);
+
+/* Operator application y = op(x) (Eq. FDE constraint matrix scaled by psi;
+ * FDE_OP_S adds the normal-equation diagonals of Eq. (generic ADMM normal
+ * equations) for the given ADMM options). Toeplitz products run by circulant
+ * embedding and FFT (Table "Complexity table", d-level Toeplitz row).
+ * precision: FDE_FP64 (x, y double*) or FDE_FP32 (float*). `opts` is read
+ * only for FDE_OP_S (delta, rho) and may be NULL otherwise. x and y must not
+ * overlap. Errors: FDE_EINVAL. */
+int fde_matvec(fde_problem* prob, int op, const fde_admm_opts* opts, int precision,
+               const void* x, void* y, void* stream);
+
+/* Preconditioner z = S~^-1 r with S~ = m1 I + C_3(B)^T C_3(B) / m2 (Eq. first
+ * schur complement preconditioner with C_3 of Eq. multilevel circulant
+ * preconditioner, J replaced by I): FFT, divide by m1 + |Lambda|^2/m2,
+ * inverse FFT. precision: FDE_FP64 (double*) or FDE_FP32 (float*). r and z
+ * may be the same array. Errors: FDE_EINVAL. */
+int fde_precond(fde_problem* prob, const fde_admm_opts* opts, int precision,
+                const void* r, void* z, void* stream);
+
+/* ADMM (Algorithm 1 with the sub-problem merged with the p update, Section 3.1,
+ * and the psi scaling of Section 6.1). Sub-problems S y = rhs are solved by
+ * PCG preconditioned with S~; in FDE_MIXED the operator and preconditioner run
+ * in float inside a double iterative-refinement loop, with the Krylov scalars,
+ * inner products, refinement residuals and ADMM residuals in double.
+ * Inputs (double, device, length N): ybar; g (NULL = 0); bounds ya, yb, ua, ub
+ * (NULL = unbounded on that side). Scalar bounds are passed as
+ * ya_s/yb_s/ua_s/ub_s and are used where the matching array pointer is NULL;
+ * give -INFINITY/+INFINITY for no bound. Outputs (double, device, length N):
+ * y, u (required), p, z_u (NULL = not returned). Iterates start at zero.
+ * stats may be NULL. Errors: FDE_EINVAL, FDE_ENOCONV (cap reached: outputs
+ * and stats hold the last iterate), FDE_EBREAKDOWN, FDE_ENONFINITE,
+ * FDE_ECUDA. Synchronises `stream`. */
+int fde_admm_solve(fde_problem* prob, const fde_admm_opts* opts,
+                   const double* ybar, const double* g,
+                   const double* ya, const double* yb, const double* ua, const double* ub,
+                   double ya_s, double yb_s, double ua_s, double ub_s,
+                   double* y, double* u, double* p, double* zu,
+                   fde_admm_stats* stats, void* stream);
+
+/* Gradient of the optimal value J* at a converged solution (envelope theorem
+ * on the Lagrangian of Eq. (Generic ADMM aug Lagrangian)):
+ *   d(J^*)/dybar = -J1 (y* - ybar)                      -> dJ_dybar (device, N, may be NULL)
+ *   d(J^*)/d{d+, d-, e+, e-} = -psi p*^T (I (x) L (x) I) y* with L = L_x, L_x^T on x1
+ *                           and L_y, L_y^T on x2       -> dJ_dcoef[4] (HOST doubles)
+ * p* is obtained by solving the adjoint equation B^T p = -J1 (y* - ybar) - w_y
+ * (w_y: the state-box multiplier, NULL = 0) with CG on B B^T preconditioned by
+ * C_3 C_3^T, to relative residual `tol` (<= 0 selects 1e-12); p_out (device, N,
+ * may be NULL) receives it. Double precision throughout. Errors: FDE_EINVAL,
+ * FDE_ENOCONV, FDE_ECUDA. Synchronises `stream`. */
+int fde_admm_grad(fde_problem* prob, const double* y, const double* ybar, const double* wy,
+                  double tol, double* dJ_dybar, double* dJ_dcoef, double* p_out, void* stream);
+
+/* Static message for a status code. */
+const char* fde_strerror(int status);
+
+/* Text of the last CUDA error seen by this library in the calling thread. */
+const char* fde_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDE_H */

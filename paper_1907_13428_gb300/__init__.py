@@ -1,0 +1,257 @@
+"""Python binding of the GB300 ADMM / Toeplitz-FFT library (include/fde.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libfde.so``. Tensors are torch CUDA tensors (device memory and the
+current stream come from PyTorch); there is no CPU fallback, and importing the
+operators raises if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfde.so")
+
+FDE_OK, FDE_EINVAL, FDE_ENOMEM, FDE_ECUDA, FDE_ENOCONV = 0, -1, -2, -3, -4
+FDE_EBREAKDOWN, FDE_ENONFINITE, FDE_EUNSUPPORTED = -5, -6, -8
+FDE_FP64, FDE_FP32, FDE_MIXED = 0, 1, 2
+FDE_OP_B, FDE_OP_BT, FDE_OP_S = 0, 1, 2
+
+
+class fde_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nt", ctypes.c_int), ("T", ctypes.c_double),
+                ("beta_x", ctypes.c_double), ("beta_y", ctypes.c_double), ("alpha_t", ctypes.c_double),
+                ("dp", ctypes.c_double), ("dm", ctypes.c_double), ("ep", ctypes.c_double), ("em", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("weights", ctypes.c_int), ("time_step_mode", ctypes.c_int)]
+
+
+class fde_admm_opts(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("rho", ctypes.c_double), ("tol_admm", ctypes.c_double),
+                ("max_admm", ctypes.c_int), ("fixed_iters", ctypes.c_int), ("max_pcg", ctypes.c_int),
+                ("inner_tol_mode", ctypes.c_int), ("inner_tol", ctypes.c_double), ("precision", ctypes.c_int),
+                ("inner_tol_mixed", ctypes.c_double), ("max_refine", ctypes.c_int)]
+
+
+class fde_admm_stats(ctypes.Structure):
+    _fields_ = [("admm_iters", ctypes.c_int), ("pcg_iters", ctypes.c_int), ("refine_steps", ctypes.c_int),
+                ("fp64_matvecs", ctypes.c_int), ("res_eq", ctypes.c_double), ("res_y", ctypes.c_double),
+                ("res_u", ctypes.c_double), ("objective", ctypes.c_double), ("max_sub_relres", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_SIGS = {
+    "fde_setup": (ctypes.c_int, [ctypes.POINTER(fde_params), ctypes.POINTER(_P), _P]),
+    "fde_destroy": (None, [_P]),
+    "fde_size": (ctypes.c_longlong, [_P]),
+    "fde_psi": (_D, [_P]),
+    "fde_matvec": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(fde_admm_opts), ctypes.c_int, _P, _P, _P]),
+    "fde_precond": (ctypes.c_int, [_P, ctypes.POINTER(fde_admm_opts), ctypes.c_int, _P, _P, _P]),
+    "fde_admm_solve": (ctypes.c_int, [_P, ctypes.POINTER(fde_admm_opts), _P, _P, _P, _P, _P, _P, _D, _D, _D, _D,
+                                      _P, _P, _P, _P, ctypes.POINTER(fde_admm_stats), _P]),
+    "fde_admm_grad": (ctypes.c_int, [_P, _P, _P, _P, _D, _P, ctypes.POINTER(ctypes.c_double), _P, _P]),
+    "fde_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "fde_last_cuda_error": (ctypes.c_char_p, []),
+}
+EXPORTED = tuple(_SIGS)
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfde.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with python -m paper_1907_13428_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class FdeError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = lib().fde_strerror(status).decode()
+        if status == FDE_ECUDA:
+            msg += ": " + lib().fde_last_cuda_error().decode()
+        super().__init__(f"{what}: {msg} ({status})")
+        self.status = status
+
+
+def _check(status: int, what: str, allow=(FDE_OK,)):
+    if status not in allow:
+        raise FdeError(status, what)
+    return status
+
+
+def _stream() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor], dtype=None, n=None):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("tensors must be contiguous CUDA tensors")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"expected {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclasses.dataclass
+class AdmmOptions:
+    delta: float = 1.0
+    rho: float = 1.618
+    tol_admm: float = 1e-6
+    max_admm: int = 1000
+    fixed_iters: bool = False
+    max_pcg: int = 1000
+    inner_tol_mode: int = 1        # 0: Section 6.1 rule, 1: fixed inner_tol
+    inner_tol: float = 1e-10
+    precision: int = FDE_FP64
+    inner_tol_mixed: float = 1e-4
+    max_refine: int = 30
+
+    def c(self) -> fde_admm_opts:
+        return fde_admm_opts(self.delta, self.rho, self.tol_admm, self.max_admm, int(self.fixed_iters), self.max_pcg,
+                             self.inner_tol_mode, self.inner_tol, self.precision, self.inner_tol_mixed,
+                             self.max_refine)
+
+
+def params_struct(p) -> fde_params:
+    """fde_params from any object with the fde_params field names."""
+    return fde_params(p.nx, p.ny, p.nt, p.T, p.beta_x, p.beta_y, p.alpha_t, p.dp, p.dm, p.ep, p.em, p.gamma,
+                      p.weights, p.time_step_mode)
+
+
+class Problem:
+    """Owner of an fde_problem handle (fde_setup / fde_destroy)."""
+
+    def __init__(self, params):
+        self.params = params
+        h = ctypes.c_void_p()
+        ps = params_struct(params)
+        _check(lib().fde_setup(ctypes.byref(ps), ctypes.byref(h), _stream()), "fde_setup")
+        self._h = h
+        self.N = int(lib().fde_size(h))
+        self.shape = (params.nt, params.nx, params.ny)
+        self.psi = float(lib().fde_psi(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fde_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def matvec(self, x: torch.Tensor, op: int = FDE_OP_B, opts: Optional[AdmmOptions] = None,
+               out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        prec = FDE_FP64 if x.dtype == torch.float64 else FDE_FP32
+        y = torch.empty_like(x) if out is None else out
+        o = (opts or AdmmOptions()).c()
+        _check(lib().fde_matvec(self._h, op, ctypes.byref(o), prec, _ptr(x, None, self.N), _ptr(y, x.dtype, self.N),
+                                _stream()), "fde_matvec")
+        return y
+
+    def precond(self, r: torch.Tensor, opts: Optional[AdmmOptions] = None,
+                out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        prec = FDE_FP64 if r.dtype == torch.float64 else FDE_FP32
+        z = torch.empty_like(r) if out is None else out
+        o = (opts or AdmmOptions()).c()
+        _check(lib().fde_precond(self._h, ctypes.byref(o), prec, _ptr(r, None, self.N), _ptr(z, r.dtype, self.N),
+                                 _stream()), "fde_precond")
+        return z
+
+    def admm_solve(self, opts: AdmmOptions, ybar: torch.Tensor, g=None, ya=None, yb=None, ua=None, ub=None,
+                   allow_noconv: bool = False, out=None):
+        """Run ADMM. Bounds may be None (unbounded), Python floats or CUDA tensors.
+        Returns dict(y, u, p, zu, stats, status)."""
+        N = self.N
+        dev = ybar.device
+
+        def bound(b, default):
+            if b is None:
+                return None, default
+            if isinstance(b, torch.Tensor):
+                return b, default
+            return None, float(b)
+
+        ya_t, ya_s = bound(ya, -math.inf)
+        yb_t, yb_s = bound(yb, math.inf)
+        ua_t, ua_s = bound(ua, -math.inf)
+        ub_t, ub_s = bound(ub, math.inf)
+        if out is None:
+            out = {k: torch.empty(N, dtype=torch.float64, device=dev) for k in ("y", "u", "p", "zu")}
+        st = fde_admm_stats()
+        o = opts.c()
+        s = lib().fde_admm_solve(self._h, ctypes.byref(o), _ptr(ybar, torch.float64, N), _ptr(g, torch.float64, N),
+                                 _ptr(ya_t, torch.float64, N), _ptr(yb_t, torch.float64, N),
+                                 _ptr(ua_t, torch.float64, N), _ptr(ub_t, torch.float64, N), ya_s, yb_s, ua_s, ub_s,
+                                 _ptr(out["y"]), _ptr(out["u"]), _ptr(out["p"]), _ptr(out["zu"]), ctypes.byref(st),
+                                 _stream())
+        _check(s, "fde_admm_solve", (FDE_OK, FDE_ENOCONV) if allow_noconv else (FDE_OK,))
+        res = dict(out)
+        res["stats"] = st.as_dict()
+        res["status"] = s
+        return res
+
+    def admm_grad(self, y: torch.Tensor, ybar: torch.Tensor, wy: Optional[torch.Tensor] = None, tol: float = 1e-12):
+        """Returns (dJ/dybar [N], dJ/d(d+, d-, e+, e-) [4] float64 CPU tensor, adjoint p [N])."""
+        N = self.N
+        dJ = torch.empty(N, dtype=torch.float64, device=y.device)
+        pv = torch.empty(N, dtype=torch.float64, device=y.device)
+        coef = (ctypes.c_double * 4)()
+        _check(lib().fde_admm_grad(self._h, _ptr(y, torch.float64, N), _ptr(ybar, torch.float64, N),
+                                   _ptr(wy, torch.float64, N), tol, _ptr(dJ), coef, _ptr(pv), _stream()),
+               "fde_admm_grad")
+        return dJ, torch.tensor(list(coef), dtype=torch.float64), pv
+
+
+class FdeAdmmFn(torch.autograd.Function):
+    """J*(ybar, d+, d-, e+, e-): optimal value of the ADMM problem. The backward
+    pass is the library's adjoint (fde_admm_grad): gradient of J* with respect
+    to the desired state and the four diffusion coefficients."""
+
+    @staticmethod
+    def forward(ctx, ybar, coef, params, opts, bounds):
+        q = dataclasses.replace(params, dp=float(coef[0]), dm=float(coef[1]), ep=float(coef[2]), em=float(coef[3]))
+        prob = Problem(q)
+        r = prob.admm_solve(opts, ybar.contiguous().view(-1), **bounds)
+        ctx.prob = prob
+        ctx.save_for_backward(r["y"], ybar)
+        return torch.tensor(r["stats"]["objective"], dtype=torch.float64, device=ybar.device)
+
+    @staticmethod
+    def backward(ctx, gout):
+        y, ybar = ctx.saved_tensors
+        dJ, dcoef, _ = ctx.prob.admm_grad(y, ybar.contiguous().view(-1))
+        ctx.prob.close()
+        return (gout * dJ.view_as(ybar), gout.cpu() * dcoef, None, None, None)
+
+
+def solve_objective(ybar: torch.Tensor, coef: torch.Tensor, params, opts: AdmmOptions, bounds: dict):
+    """Differentiable optimal value (see FdeAdmmFn)."""
+    return FdeAdmmFn.apply(ybar, coef, params, opts, bounds)

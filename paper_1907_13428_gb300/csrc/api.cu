@@ -1,0 +1,526 @@
+// C ABI entry points (include/fde.h): problem set-up, operator and
+// preconditioner applications, the PCG / iterative-refinement sub-solves and
+// the ADMM driver (Algorithm 1 with the sub-problem merged with the p update,
+// Section 3.1; psi scaling and stopping rules of Section 6.1), and the
+// gradient of the optimal value.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.h"
+#include "vec.h"
+
+using namespace fde;
+
+static thread_local char g_cuda_err[256] = "";
+
+cudaError_t fde_alloc(fde_problem* P, void** ptr, size_t bytes) {
+  if (P->nallocs >= (int)(sizeof(P->allocs) / sizeof(P->allocs[0]))) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
+  if (e == cudaSuccess) P->allocs[P->nallocs++] = *ptr;
+  return e;
+}
+
+static int cuda_status(cudaError_t e) {
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? FDE_ENOMEM : FDE_ECUDA;
+}
+
+#define CK(expr)                                 \
+  do {                                           \
+    cudaError_t _e = (expr);                     \
+    if (_e != cudaSuccess) return cuda_status(_e); \
+  } while (0)
+
+#define RK(expr)                 \
+  do {                           \
+    int _s = (expr);             \
+    if (_s != FDE_OK) return _s; \
+  } while (0)
+
+// FP64 workspace slots
+enum {
+  V_Y = 0, V_U, V_ZY, V_ZU, V_P, V_WY, V_WU, V_C, V_BU, V_R0, V_Q, V_RHS, V_BY, V_R, V_Z, V_D, V_SD, V_W, V_T1, V_T2,
+  V_COUNT
+};
+// FP32 workspace slots
+enum { F_B = 0, F_X, F_R, F_Z, F_D, F_Q, F_W, F_T1, F_T2, F_COUNT };
+
+namespace {
+
+struct Diags {
+  SliceDiag w, M1, Q, M2, M2inv;
+  double m1, m2;  // preconditioner scalars (J ~ I)
+};
+
+Diags make_diags(const fde_problem* P, double delta, double rho) {
+  Diags d{};
+  const double psi2 = P->psi * P->psi;
+  d.w.v[0] = 1.0;
+  d.w.v[1] = P->prm.weights == 0 ? 0.5 : 1.0;
+  for (int s = 0; s < 2; ++s) {
+    d.M1.v[s] = rho * (d.w.v[s] + 1.0 / delta);
+    d.Q.v[s] = rho * (P->prm.gamma * d.w.v[s] + psi2 / delta);
+    d.M2.v[s] = psi2 / d.Q.v[s] + delta / rho;
+    d.M2inv.v[s] = 1.0 / d.M2.v[s];
+  }
+  d.m1 = rho * (1.0 + 1.0 / delta);
+  d.m2 = psi2 / (rho * (P->prm.gamma + psi2 / delta)) + delta / rho;
+  return d;
+}
+
+bool valid_opts(const fde_admm_opts* o) {
+  if (!o) return false;
+  const double golden = (1.0 + std::sqrt(5.0)) / 2.0;
+  return std::isfinite(o->delta) && o->delta > 0 && std::isfinite(o->rho) && o->rho > 0 && o->rho < golden;
+}
+
+int read_scalars(fde_problem* P, cudaStream_t st) {
+  CK(cudaMemcpyAsync(P->hscal, P->dscal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const int flag = (int)P->hscal[S_FLAG];
+  return flag;  // 0 or a negative FDE status
+}
+
+int clear_flag(fde_problem* P, cudaStream_t st) {
+  CK(cudaMemsetAsync(P->dscal + S_FLAG, 0, sizeof(double), st));
+  return FDE_OK;
+}
+
+template <typename R> cplx<R>* spec(fde_problem* P);
+template <> double2* spec<double>(fde_problem* P) { return P->spec64; }
+template <> float2* spec<float>(fde_problem* P) { return P->spec32; }
+
+// Scratch triple (w, tmp1, tmp2) of each precision for operator applications.
+template <typename R> struct Scratch { R *w, *t1, *t2; };
+Scratch<double> scratch64(fde_problem* P) { return {P->v64[V_W], P->v64[V_T1], P->v64[V_T2]}; }
+Scratch<float> scratch32(fde_problem* P) { return {P->v32[F_W], P->v32[F_T1], P->v32[F_T2]}; }
+
+// Preconditioned CG (the MATLAB pcg recurrence, Hestenes-Stiefel form) on an
+// SPD operator `A` with preconditioner `M`; scalars and inner products in
+// double on the device. Stops when ||r||_2 <= tol ||b||_2 (recursive residual).
+// x holds the initial guess when x_zero == false (double vectors only).
+template <typename R, class OpA, class OpM>
+int pcg(fde_problem* P, OpA A, OpM M, const R* b, R* x, bool x_zero, double tol, int maxit, R* r, R* z, R* d, R* q,
+        cudaStream_t st, int* iters, double* relres) {
+  const long long N = P->N;
+  *iters = 0;
+  RK(clear_flag(P, st));
+  CK((dot<R, R>(P, b, b, N, S_BB, FIN_STORE, st)));
+  if (x_zero) {
+    CK(fill<R>(x, (R)0, N, st));
+    CK(copy<R>(r, b, N, st));
+    CK((dot<R, R>(P, r, r, N, S_RR, FIN_STORE, st)));
+  } else {
+    RK(A(x, q));
+    if constexpr (sizeof(R) == 8) {
+      CK(residual(P, (const double*)b, (const double*)q, (double*)r, N, S_RR, st));
+    } else {
+      return FDE_EINVAL;
+    }
+  }
+  int flag = read_scalars(P, st);
+  if (flag < 0) return flag;
+  const double bb = P->hscal[S_BB];
+  double rr = P->hscal[S_RR];
+  if (bb == 0.0) {
+    CK(fill<R>(x, (R)0, N, st));
+    *relres = 0.0;
+    return FDE_OK;
+  }
+  const double thr = tol * tol * bb;
+  if (rr <= thr) {
+    *relres = std::sqrt(rr / bb);
+    return FDE_OK;
+  }
+  RK(M(r, z));
+  CK((dot<R, R>(P, r, z, N, 0, FIN_RZ0, st)));
+  CK(copy<R>(d, z, N, st));
+  for (int it = 1; it <= maxit; ++it) {
+    RK(A(d, q));
+    CK((dot<R, R>(P, d, q, N, 0, FIN_ALPHA, st)));
+    CK(pcg_xr<R>(P, x, r, d, q, N, st));
+    flag = read_scalars(P, st);
+    if (flag < 0) return flag;
+    rr = P->hscal[S_RR];
+    *iters = it;
+    if (rr <= thr) {
+      *relres = std::sqrt(rr / bb);
+      return FDE_OK;
+    }
+    RK(M(r, z));
+    CK((dot<R, R>(P, r, z, N, 0, FIN_BETA, st)));
+    CK(pcg_p<R>(P, d, z, N, st));
+  }
+  *relres = std::sqrt(rr / bb);
+  return FDE_ENOCONV;
+}
+
+template <typename R>
+int op_S(fde_problem* P, const Diags& dg, const R* x, R* y, Scratch<R> s, cudaStream_t st) {
+  CK(apply_S<R>(P, dg.M1, dg.M2inv, x, y, s.w, s.t1, s.t2, st));
+  return FDE_OK;
+}
+template <typename R>
+int op_M(fde_problem* P, const Diags& dg, const R* r, R* z, cudaStream_t st) {
+  CK(apply_precond<R>(P, dg.m1, dg.m2, 0, r, z, spec<R>(P), st));
+  return FDE_OK;
+}
+
+struct SolveInfo {
+  int pcg_iters = 0, refine = 0, fp64_matvecs = 0;
+  double relres = 0.0;
+};
+
+// Solve S y = rhs, y holding a warm start. FP64: PCG in double. MIXED: double
+// iterative refinement around float PCG on the correction.
+int subsolve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const double* rhs, double* y, double tol,
+             cudaStream_t st, SolveInfo* info) {
+  const long long N = P->N;
+  if (o->precision == FDE_FP64) {
+    auto A = [&](const double* x, double* out) { return op_S<double>(P, dg, x, out, scratch64(P), st); };
+    auto M = [&](const double* r, double* z) { return op_M<double>(P, dg, r, z, st); };
+    int it = 0;
+    double rel = 0;
+    const int s = pcg<double>(P, A, M, rhs, y, false, tol, o->max_pcg, P->v64[V_R], P->v64[V_Z], P->v64[V_D],
+                              P->v64[V_SD], st, &it, &rel);
+    info->pcg_iters += it;
+    info->fp64_matvecs += 2 * (it + 1);
+    info->relres = rel;
+    return s;
+  }
+  // mixed
+  CK((dot<double, double>(P, rhs, rhs, N, S_TMP0, FIN_STORE, st)));
+  int flag = read_scalars(P, st);
+  if (flag < 0) return flag;
+  const double bb = P->hscal[S_TMP0];
+  if (bb == 0.0) {
+    CK(fill<double>(y, 0.0, N, st));
+    info->relres = 0.0;
+    return FDE_OK;
+  }
+  const double inner = o->inner_tol_mixed > 0 ? o->inner_tol_mixed : 1e-4;
+  const int maxref = o->max_refine > 0 ? o->max_refine : 20;
+  auto A32 = [&](const float* x, float* out) { return op_S<float>(P, dg, x, out, scratch32(P), st); };
+  auto M32 = [&](const float* r, float* z) { return op_M<float>(P, dg, r, z, st); };
+  for (int k = 0; k <= maxref; ++k) {
+    RK(op_S<double>(P, dg, y, P->v64[V_SD], scratch64(P), st));
+    info->fp64_matvecs += 2;
+    CK(residual(P, rhs, P->v64[V_SD], P->v64[V_R], N, S_RR, st));
+    flag = read_scalars(P, st);
+    if (flag < 0) return flag;
+    const double rel = std::sqrt(P->hscal[S_RR] / bb);
+    info->relres = rel;
+    if (rel <= tol) return FDE_OK;
+    if (k == maxref) break;
+    CK(to_f32(P->v64[V_R], P->v32[F_B], N, st));
+    int it = 0;
+    double rr32 = 0;
+    // the float correction only needs to reduce the residual by `inner`
+    const int s = pcg<float>(P, A32, M32, P->v32[F_B], P->v32[F_X], true, std::fmax(inner, tol / rel * 0.5),
+                             o->max_pcg, P->v32[F_R], P->v32[F_Z], P->v32[F_D], P->v32[F_Q], st, &it, &rr32);
+    info->pcg_iters += it;
+    info->refine += 1;
+    if (s != FDE_OK && s != FDE_ENOCONV) return s;
+    CK(add_f32(y, P->v32[F_X], N, st));
+  }
+  return FDE_ENOCONV;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fde_strerror(int s) {
+  switch (s) {
+    case FDE_OK: return "ok";
+    case FDE_EINVAL: return "invalid argument";
+    case FDE_ENOMEM: return "device out of memory";
+    case FDE_ECUDA: return "CUDA error";
+    case FDE_ENOCONV: return "iteration cap reached before convergence";
+    case FDE_EBREAKDOWN: return "PCG breakdown (non-positive curvature)";
+    case FDE_ENONFINITE: return "non-finite value in a reduction";
+    case FDE_EUNSUPPORTED: return "unsupported size or mode";
+    default: return "unknown status";
+  }
+}
+
+const char* fde_last_cuda_error(void) { return g_cuda_err; }
+
+long long fde_size(const fde_problem* P) { return P ? P->N : 0; }
+double fde_psi(const fde_problem* P) { return P ? P->psi : 0.0; }
+
+void fde_destroy(fde_problem* P) {
+  if (!P) return;
+  for (int i = 0; i < P->nallocs; ++i) cudaFree(P->allocs[i]);
+  if (P->hscal) cudaFreeHost(P->hscal);
+  delete P;
+}
+
+int fde_setup(const fde_params* prm, fde_problem** out, void* stream) {
+  if (!prm || !out) return FDE_EINVAL;
+  *out = nullptr;
+  const fde_params& q = *prm;
+  auto fin = [](double v) { return std::isfinite(v); };
+  if (q.nx < 1 || q.ny < 1 || q.nt < 1) return FDE_EINVAL;
+  if (!(fin(q.beta_x) && q.beta_x > 1 && q.beta_x < 2 && fin(q.beta_y) && q.beta_y > 1 && q.beta_y < 2))
+    return FDE_EINVAL;
+  if (!(fin(q.alpha_t) && q.alpha_t > 0 && q.alpha_t <= 1)) return FDE_EINVAL;
+  if (!(fin(q.dp) && fin(q.dm) && fin(q.ep) && fin(q.em) && q.dp >= 0 && q.dm >= 0 && q.ep >= 0 && q.em >= 0))
+    return FDE_EINVAL;
+  if (!(fin(q.gamma) && q.gamma > 0)) return FDE_EINVAL;
+  if (!(fin(q.T) && q.T > 0)) return FDE_EINVAL;
+  if ((q.weights != 0 && q.weights != 1) || (q.time_step_mode != 0 && q.time_step_mode != 1)) return FDE_EINVAL;
+  if (q.nx > kMaxAxis || q.ny > kMaxAxis || q.nt > kMaxAxis) return FDE_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  static bool attrs_done = false;
+  if (!attrs_done) {
+    CK(toeplitz_set_smem_attrs());
+    CK(precond_set_smem_attrs());
+    attrs_done = true;
+  }
+
+  fde_problem* P = new fde_problem();
+  P->prm = q;
+  P->nx = q.nx;
+  P->ny = q.ny;
+  P->nt = q.nt;
+  P->N = (long long)q.nx * q.ny * q.nt;
+  P->hx = 1.0 / (q.nx + 1);
+  P->hy = 1.0 / (q.ny + 1);
+  P->ht = q.time_step_mode == 0 ? q.T / q.nt : P->hx;
+  P->psi = std::fmin(std::pow(P->ht, q.alpha_t), std::fmin(std::pow(P->hx, q.beta_x), std::pow(P->hy, q.beta_y)));
+  P->euler = (q.alpha_t == 1.0);
+  P->H = q.ny / 2 + 1;
+  P->Hp = (P->H + 1) & ~1;
+
+  auto fail = [&](cudaError_t e) {
+    const int s = cuda_status(e);
+    fde_destroy(P);
+    return s;
+  };
+  cudaError_t e;
+  if ((e = cudaMallocHost((void**)&P->hscal, sizeof(double) * S_COUNT))) return fail(e);
+  void* p;
+  if ((e = fde_alloc(P, &p, sizeof(double) * kMaxPartials))) return fail(e);
+  P->partials = (double*)p;
+  if ((e = fde_alloc(P, &p, sizeof(double) * S_COUNT))) return fail(e);
+  P->dscal = (double*)p;
+  if ((e = cudaMemsetAsync(P->dscal, 0, sizeof(double) * S_COUNT, st))) return fail(e);
+  if ((e = setup_axis_tables(P, st))) return fail(e);
+  const size_t N = (size_t)P->N;
+  for (int i = 0; i < V_COUNT; ++i) {
+    if ((e = fde_alloc(P, &p, sizeof(double) * N))) return fail(e);
+    P->v64[i] = (double*)p;
+    if ((e = cudaMemsetAsync(p, 0, sizeof(double) * N, st))) return fail(e);
+  }
+  for (int i = 0; i < F_COUNT; ++i) {
+    if ((e = fde_alloc(P, &p, sizeof(float) * N))) return fail(e);
+    P->v32[i] = (float*)p;
+    if ((e = cudaMemsetAsync(p, 0, sizeof(float) * N, st))) return fail(e);
+  }
+  const size_t ns = (size_t)P->nt * P->nx * P->Hp;
+  if ((e = fde_alloc(P, &p, sizeof(double2) * ns))) return fail(e);
+  P->spec64 = (double2*)p;
+  if ((e = cudaMemsetAsync(p, 0, sizeof(double2) * ns, st))) return fail(e);
+  if ((e = fde_alloc(P, &p, sizeof(float2) * ns))) return fail(e);
+  P->spec32 = (float2*)p;
+  if ((e = cudaMemsetAsync(p, 0, sizeof(float2) * ns, st))) return fail(e);
+  if ((e = cudaStreamSynchronize(st))) return fail(e);
+  *out = P;
+  return FDE_OK;
+}
+
+int fde_matvec(fde_problem* P, int op, const fde_admm_opts* o, int precision, const void* x, void* y, void* stream) {
+  if (!P || !x || !y || x == y) return FDE_EINVAL;
+  if (op != FDE_OP_B && op != FDE_OP_BT && op != FDE_OP_S) return FDE_EINVAL;
+  if (precision != FDE_FP64 && precision != FDE_FP32) return FDE_EINVAL;
+  if (op == FDE_OP_S && !valid_opts(o)) return FDE_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == FDE_FP64) {
+    auto s = scratch64(P);
+    if (op == FDE_OP_S) {
+      const Diags dg = make_diags(P, o->delta, o->rho);
+      return op_S<double>(P, dg, (const double*)x, (double*)y, s, st);
+    }
+    CK(apply_B<double>(P, op == FDE_OP_BT, (const double*)x, (double*)y, nullptr, nullptr, nullptr, s.t1, s.t2, st));
+  } else {
+    auto s = scratch32(P);
+    if (op == FDE_OP_S) {
+      const Diags dg = make_diags(P, o->delta, o->rho);
+      return op_S<float>(P, dg, (const float*)x, (float*)y, s, st);
+    }
+    CK(apply_B<float>(P, op == FDE_OP_BT, (const float*)x, (float*)y, nullptr, nullptr, nullptr, s.t1, s.t2, st));
+  }
+  return FDE_OK;
+}
+
+int fde_precond(fde_problem* P, const fde_admm_opts* o, int precision, const void* r, void* z, void* stream) {
+  if (!P || !r || !z || !valid_opts(o)) return FDE_EINVAL;
+  if (precision != FDE_FP64 && precision != FDE_FP32) return FDE_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (!P->ax[a].n_ok) return FDE_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Diags dg = make_diags(P, o->delta, o->rho);
+  if (precision == FDE_FP64) return op_M<double>(P, dg, (const double*)r, (double*)z, st);
+  return op_M<float>(P, dg, (const float*)r, (float*)z, st);
+}
+
+int fde_admm_solve(fde_problem* P, const fde_admm_opts* o, const double* ybar, const double* g, const double* ya,
+                   const double* yb, const double* ua, const double* ub, double ya_s, double yb_s, double ua_s,
+                   double ub_s, double* y, double* u, double* p, double* zu, fde_admm_stats* stats, void* stream) {
+  if (!P || !valid_opts(o) || !ybar || !y || !u) return FDE_EINVAL;
+  if (o->precision != FDE_FP64 && o->precision != FDE_MIXED) return FDE_EINVAL;
+  if (o->max_admm < 1 || o->max_pcg < 1) return FDE_EINVAL;
+  if (std::isnan(ya_s) || std::isnan(yb_s) || std::isnan(ua_s) || std::isnan(ub_s)) return FDE_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (!P->ax[a].n_ok) return FDE_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long N = P->N;
+  const Diags dg = make_diags(P, o->delta, o->rho);
+
+  AdmmArgs A{};
+  A.n = N;
+  A.last_start = (long long)(P->nt - 1) * P->nx * P->ny;
+  A.rho = o->rho;
+  A.delta = o->delta;
+  A.inv_delta = 1.0 / o->delta;
+  A.rho_over_delta = o->rho / o->delta;
+  A.delta_over_rho = o->delta / o->rho;
+  A.psi = P->psi;
+  A.gamma = P->prm.gamma;
+  for (int s = 0; s < 2; ++s) {
+    A.w[s] = dg.w.v[s];
+    A.Q[s] = dg.Q.v[s];
+    A.M2[s] = dg.M2.v[s];
+  }
+  A.ybar = ybar;
+  A.g = g;
+  A.ya = ya;
+  A.yb = yb;
+  A.ua = ua;
+  A.ub = ub;
+  A.ya_s = ya_s;
+  A.yb_s = yb_s;
+  A.ua_s = ua_s;
+  A.ub_s = ub_s;
+  double* Y = P->v64[V_Y];
+  double* U = P->v64[V_U];
+  A.zy = P->v64[V_ZY];
+  A.zu = P->v64[V_ZU];
+  A.p = P->v64[V_P];
+  A.wy = P->v64[V_WY];
+  A.wu = P->v64[V_WU];
+  for (int i : {V_Y, V_U, V_ZY, V_ZU, V_P, V_WY, V_WU}) CK(fill<double>(P->v64[i], 0.0, N, st));
+
+  fde_admm_stats S{};
+  SolveInfo info;
+  double res[3] = {1.0, 1.0, 1.0};
+  int status = FDE_ENOCONV;
+  auto s64 = scratch64(P);
+  const SliceDiag one{{1.0, 1.0}};
+  for (int j = 0; j < o->max_admm; ++j) {
+    CK(admm_pre(A, P->v64[V_C], P->v64[V_BU], P->v64[V_R0], P->v64[V_Q], st));
+    // rhs = c + B^T q
+    CK(apply_B<double>(P, 1, P->v64[V_Q], P->v64[V_RHS], nullptr, P->v64[V_C], &one, s64.t1, s64.t2, st));
+    info.fp64_matvecs += 1;
+    double tol;
+    if (o->inner_tol_mode == 1) {
+      tol = o->inner_tol;
+    } else {
+      const double mn = std::fmin(res[0], std::fmin(res[1], res[2]));
+      tol = 0.05 * std::fmax(mn, o->tol_admm);
+    }
+    const int s = subsolve(P, dg, o, P->v64[V_RHS], Y, tol, st, &info);
+    if (s != FDE_OK && s != FDE_ENOCONV) {
+      status = s;
+      break;
+    }
+    S.max_sub_relres = std::fmax(S.max_sub_relres, info.relres);
+    CK(apply_B<double>(P, 0, Y, P->v64[V_BY], nullptr, nullptr, nullptr, s64.t1, s64.t2, st));
+    info.fp64_matvecs += 1;
+    RK(clear_flag(P, st));
+    CK(admm_post(P, A, Y, P->v64[V_BY], P->v64[V_BU], P->v64[V_R0], U, st));
+    const int flag = read_scalars(P, st);
+    S.admm_iters = j + 1;
+    res[0] = P->hscal[S_RES_EQ];
+    res[1] = P->hscal[S_RES_Y];
+    res[2] = P->hscal[S_RES_U];
+    S.objective = P->hscal[S_OBJ];
+    if (flag < 0) {
+      status = flag;
+      break;
+    }
+    if (o->fixed_iters) {
+      status = FDE_OK;
+      continue;
+    }
+    if (res[0] <= o->tol_admm && res[1] <= o->tol_admm && res[2] <= o->tol_admm) {
+      status = FDE_OK;
+      break;
+    }
+  }
+  S.pcg_iters = info.pcg_iters;
+  S.refine_steps = info.refine;
+  S.fp64_matvecs = info.fp64_matvecs;
+  S.res_eq = res[0];
+  S.res_y = res[1];
+  S.res_u = res[2];
+  CK(cudaMemcpyAsync(y, Y, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(u, U, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  if (p) CK(cudaMemcpyAsync(p, A.p, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  if (zu) CK(cudaMemcpyAsync(zu, A.zu, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  if (stats) *stats = S;
+  return status;
+}
+
+int fde_admm_grad(fde_problem* P, const double* y, const double* ybar, const double* wy, double tol, double* dJ_dybar,
+                  double* dJ_dcoef, double* p_out, void* stream) {
+  if (!P || !y || !ybar || !dJ_dcoef) return FDE_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (!P->ax[a].n_ok) return FDE_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long N = P->N;
+  if (!(tol > 0)) tol = 1e-12;
+  const double w1 = P->prm.weights == 0 ? 0.5 : 1.0;
+  double* f = P->v64[V_C];
+  double* rhs = P->v64[V_RHS];
+  double* pv = P->v64[V_P];
+  auto s = scratch64(P);
+  // f = -J1 (y - ybar) - w_y
+  CK(grad_ybar(y, ybar, wy, 1.0, w1, (long long)(P->nt - 1) * P->nx * P->ny, N, dJ_dybar, f, st));
+  // B B^T p = B f
+  CK(apply_B<double>(P, 0, f, rhs, nullptr, nullptr, nullptr, s.t1, s.t2, st));
+  auto A = [&](const double* x, double* out) -> int {
+    CK(apply_B<double>(P, 1, x, s.w, nullptr, nullptr, nullptr, s.t1, s.t2, st));
+    CK(apply_B<double>(P, 0, s.w, out, nullptr, nullptr, nullptr, s.t1, s.t2, st));
+    return FDE_OK;
+  };
+  auto M = [&](const double* r, double* z) -> int {
+    CK(apply_precond<double>(P, 0.0, 1.0, 1, r, z, P->spec64, st));
+    return FDE_OK;
+  };
+  int it = 0;
+  double rel = 0;
+  const int sres = pcg<double>(P, A, M, rhs, pv, true, tol, 5000, P->v64[V_R], P->v64[V_Z], P->v64[V_D],
+                               P->v64[V_SD], st, &it, &rel);
+  if (sres != FDE_OK) return sres;
+  // dJ/d{d+, d-} along x1 with L_x, L_x^T; dJ/d{e+, e-} along x2 with L_y, L_y^T
+  double* t = P->v64[V_Q];
+  for (int c = 0; c < 4; ++c) {
+    const int axis = c < 2 ? 1 : 2;
+    // the conjugate symbol gives L^T
+    CK(apply_axis_raw<double>(P, axis, y, t, P->ax[axis].d.symL, c % 2, st));
+    CK((dot<double, double>(P, pv, t, N, S_TMP0 + 0, FIN_STORE, st)));
+    const int flag = read_scalars(P, st);
+    if (flag < 0) return flag;
+    dJ_dcoef[c] = -P->psi * P->hscal[S_TMP0];
+  }
+  if (p_out) CK(cudaMemcpyAsync(p_out, pv, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return FDE_OK;
+}
+
+}  // extern "C"

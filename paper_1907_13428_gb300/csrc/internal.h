@@ -1,0 +1,101 @@
+// Internal host-side declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/fde.h"
+#include "common.cuh"
+
+namespace fde {
+
+constexpr int kMaxAxis = 4096;
+
+// Device tables of one axis in one precision.
+template <typename R> struct AxisTables {
+  cplx<R>* sym = nullptr;  // [2][L]: halves lambda_emb[2k+s] of the circulant embedding symbol,
+                           //         pre-scaled by coef/(2L) (coef = -psi in space, +psi in time)
+  cplx<R>* tw2 = nullptr;  // W_{2L}^m, m in [0, 2L): pre/post twists of the odd half
+  cplx<R>* twL = nullptr;  // W_L^m, m in [0, L): FFT table of the embedding length
+  cplx<R>* lam = nullptr;  // T. Chan circulant eigenvalues, length n (unscaled)
+  cplx<R>* twn = nullptr;  // W_n^m, m in [0, n): FFT table of the exact length
+  cplx<R>* symL = nullptr; // [2][L]: embedding symbol halves of the one-sided L alone,
+                           //         scaled by 1/(2L) (space axes, double only; gradient)
+};
+
+struct Axis {
+  int n = 0;        // points on this axis
+  int L = 0;        // embedding half-length: smallest power of two >= n
+  FftPlan planL{};  // radix plan of L
+  FftPlan plann{};  // radix plan of n (preconditioner)
+  bool n_ok = false;  // n factors into 2, 3, 5, 7
+  AxisTables<double> d;
+  AxisTables<float> f;
+};
+
+// Per-time-slice diagonal: value on slices 0..nt-2 and on the last slice.
+struct SliceDiag {
+  double v[2];
+};
+
+}  // namespace fde
+
+struct fde_problem {
+  fde_params prm;
+  long long N = 0;
+  int nx = 0, ny = 0, nt = 0;
+  double hx = 0, hy = 0, ht = 0, psi = 0;
+  bool euler = true;   // alpha_t == 1: the time term is the two-point backward difference
+  int H = 0, Hp = 0;   // half-spectrum length ny/2+1 and its padded row stride
+  fde::Axis ax[3];     // 0: time, 1: x1, 2: x2
+  // workspace (device)
+  double* v64[24] = {};
+  float* v32[12] = {};
+  double2* spec64 = nullptr;
+  float2* spec32 = nullptr;
+  double* partials = nullptr;  // reduction partial sums
+  double* dscal = nullptr;     // device scalars
+  double* hscal = nullptr;     // pinned host mirror of a few scalars
+  int npartials = 0;
+  void* allocs[96] = {};
+  int nallocs = 0;
+};
+
+namespace fde {
+
+// Device-scalar slots in fde_problem::dscal.
+enum Scal {
+  S_RZ = 0, S_RZ_NEW, S_PQ, S_ALPHA, S_BETA, S_RR, S_BB, S_TMP0, S_TMP1, S_TMP2,
+  S_RES_EQ, S_RES_Y, S_RES_U, S_OBJ, S_FLAG, S_COUNT = 32
+};
+
+// ---- launchers (each returns cudaError_t of the launch) ----
+
+// Set-up of the axis tables (setup.cu).
+cudaError_t setup_axis_tables(fde_problem* P, cudaStream_t st);
+
+// Toeplitz operator passes (toeplitz.cu).
+//   op: 0 = B, 1 = B^T. If dscale != null the result is multiplied per slice
+//   (M2^-1 for S). If addv != null, addc(t) * addv is added after that.
+template <typename R>
+cudaError_t apply_B(fde_problem* P, int transpose, const R* x, R* y, const SliceDiag* dscale,
+                    const R* addv, const SliceDiag* addc, R* tmp1, R* tmp2, cudaStream_t st);
+// y = S x = M1 x + B^T (M2^-1 B x), using w (N) and tmp1, tmp2 (N) as scratch.
+template <typename R>
+cudaError_t apply_S(fde_problem* P, const SliceDiag& M1, const SliceDiag& M2inv, const R* x, R* y,
+                    R* w, R* tmp1, R* tmp2, cudaStream_t st);
+// One spatial factor along one axis (1: x1, 2: x2) with the given symbol
+// halves (e.g. AxisTables::symL for the one-sided L), no time term, for the gradient.
+template <typename R>
+cudaError_t apply_axis_raw(fde_problem* P, int axis, const R* x, R* y, const cplx<R>* sym, int conj_sym,
+                           cudaStream_t st);
+
+// Preconditioner (precond.cu): z = S~^-1 r (r and z may alias). mode 0: S~
+// (m1, m2); mode 1: (C3 C3^T)^-1 (the adjoint normal-equation preconditioner).
+template <typename R>
+cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const R* r, R* z,
+                          cplx<R>* spec, cudaStream_t st);
+
+
+}  // namespace fde

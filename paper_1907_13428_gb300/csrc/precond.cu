@@ -1,0 +1,255 @@
+// Multilevel circulant preconditioner (Section 5, Eq. multilevel circulant
+// preconditioner, and Eq. first schur complement preconditioner with J ~ I):
+//   z = F^-1 diag(1/sigma) F r,  sigma[k,i,j] = m1 + |Lambda[k,i,j]|^2 / m2,
+//   Lambda = psi (lambda_t[k] - lambda_x[i] - lambda_y[j]),
+// where lambda_* are the DFTs of the T. Chan circulants of C_t, X and Y and F
+// is the three-level DFT (transform order is irrelevant: the levels commute).
+// Mode 1 replaces sigma by |Lambda|^2, which is (C_3 C_3^T)^-1 for the adjoint
+// solve of the gradient.
+//
+// Data path (r real, N = nt*nx*ny):
+//   1. x2 rows: two real rows form one complex line; after the order-ny DFT the
+//      half spectra of both rows (ny/2+1 bins) are separated and stored in
+//      spec[t][x1][Hp] (Hp = padded row stride);
+//   2. x1 columns of spec: forward DFT;
+//   3. t columns of spec: forward DFT, divide by N*sigma, inverse DFT;
+//   4. x1 columns: inverse DFT;
+//   5. x2 rows: the two Hermitian half spectra are recombined into one complex
+//      line, inverse DFT, real and imaginary parts are the two output rows.
+#include "internal.h"
+
+namespace fde {
+
+constexpr int kPEPT = 16;
+
+template <typename R> static const AxisTables<R>& ptables(const Axis& A);
+template <> const AxisTables<double>& ptables<double>(const Axis& A) { return A.d; }
+template <> const AxisTables<float>& ptables<float>(const Axis& A) { return A.f; }
+
+// Step 1: rows of r -> half spectra.
+template <typename R>
+__global__ void __launch_bounds__(512) k_prec_rows_fwd(const R* __restrict__ r, cplx<R>* __restrict__ spec,
+                                                        long long nrows, int n, int H, int Hp,
+                                                        const cplx<R>* __restrict__ twn, FftPlan pl, int pairs) {
+  using C = cplx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const long long row0 = (long long)blockIdx.x * pairs * 2;
+  for (int e = threadIdx.x; e < pairs * n; e += blockDim.x) {
+    const int p = e / n, j = e - p * n;
+    const long long ra = row0 + 2 * p, rb = ra + 1;
+    const R a = ra < nrows ? r[ra * n + j] : (R)0;
+    const R b = rb < nrows ? r[rb * n + j] : (R)0;
+    buf[p * n + j] = mk<C>(a, b);
+  }
+  __syncthreads();
+  smem_fft<R, kPEPT>(buf, pairs, n, pl, twn, false);
+  for (int e = threadIdx.x; e < pairs * H; e += blockDim.x) {
+    const int p = e / H, k = e - p * H;
+    const long long ra = row0 + 2 * p, rb = ra + 1;
+    const C zk = buf[p * n + k];
+    const C zm = cconj(buf[p * n + (k == 0 ? 0 : n - k)]);
+    // A = (Z_k + conj Z_{-k}) / 2,  B = (Z_k - conj Z_{-k}) / (2i)
+    const C A = mk<C>((zk.x + zm.x) * (R)0.5, (zk.y + zm.y) * (R)0.5);
+    const C D = mk<C>((zk.x - zm.x) * (R)0.5, (zk.y - zm.y) * (R)0.5);
+    const C B = mk<C>(D.y, -D.x);
+    if (ra < nrows) spec[ra * Hp + k] = A;
+    if (rb < nrows) spec[rb * Hp + k] = B;
+  }
+}
+
+// Step 5: half spectra -> rows of z.
+template <typename R>
+__global__ void __launch_bounds__(512) k_prec_rows_inv(const cplx<R>* __restrict__ spec, R* __restrict__ z,
+                                                        long long nrows, int n, int H, int Hp,
+                                                        const cplx<R>* __restrict__ twn, FftPlan pl, int pairs) {
+  using C = cplx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const long long row0 = (long long)blockIdx.x * pairs * 2;
+  for (int e = threadIdx.x; e < pairs * n; e += blockDim.x) {
+    const int p = e / n, k = e - p * n;
+    const long long ra = row0 + 2 * p, rb = ra + 1;
+    const bool lo = k < H;
+    const int kk = lo ? k : n - k;
+    C A = ra < nrows ? spec[ra * Hp + kk] : mk<C>(0, 0);
+    C B = rb < nrows ? spec[rb * Hp + kk] : mk<C>(0, 0);
+    if (!lo) {
+      A = cconj(A);
+      B = cconj(B);
+    }
+    buf[p * n + k] = mk<C>(A.x - B.y, A.y + B.x);  // A + i B
+  }
+  __syncthreads();
+  smem_fft<R, kPEPT>(buf, pairs, n, pl, twn, true);
+  for (int e = threadIdx.x; e < pairs * n; e += blockDim.x) {
+    const int p = e / n, j = e - p * n;
+    const long long ra = row0 + 2 * p, rb = ra + 1;
+    const C v = buf[p * n + j];
+    if (ra < nrows) z[ra * n + j] = v.x;
+    if (rb < nrows) z[rb * n + j] = v.y;
+  }
+}
+
+// Steps 2-4: complex columns of spec along an axis (x1: stride Hp inside each
+// time slice; t: stride nx*Hp). mode: 0 forward, 1 inverse, 2 forward, divide
+// by sigma*N (or |Lambda|^2 * N), inverse.
+struct DivArgs {
+  int divide;     // 1 on the time pass
+  int adjoint;    // 1: sigma = |Lambda|^2
+  double m1, inv_m2, psi, inv_N;
+  int Hp, H;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(1024) k_prec_axis(cplx<R>* __restrict__ spec, int n, long long axis_stride,
+                                                     long long n_inner, long long outer_stride, long long n_outer,
+                                                     const cplx<R>* __restrict__ twn, FftPlan pl, int inverse,
+                                                     int lines, DivArgs dv, const cplx<R>* __restrict__ lt,
+                                                     const cplx<R>* __restrict__ lx, const cplx<R>* __restrict__ ly) {
+  using C = cplx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const long long total = n_outer * n_inner;
+  const long long l0 = (long long)blockIdx.x * lines;
+  for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+    const int a = e / lines, l = e - a * lines;
+    const long long q = l0 + l;
+    C v = mk<C>(0, 0);
+    if (q < total) {
+      const long long o = q / n_inner, c = q - o * n_inner;
+      v = spec[o * outer_stride + c + a * axis_stride];
+    }
+    buf[l * n + a] = v;
+  }
+  __syncthreads();
+  smem_fft<R, kPEPT>(buf, lines, n, pl, twn, dv.divide ? false : (inverse != 0));
+  if (dv.divide) {
+    for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+      const int l = e / n, k = e - l * n;
+      const long long q = l0 + l;
+      if (q >= total) continue;
+      const long long c = q % n_inner;  // = i*Hp + j within a time slice
+      const int i = (int)(c / dv.Hp), j = (int)(c - (long long)i * dv.Hp);
+      if (j >= dv.H) continue;  // padding column: stays zero
+      const C a = __ldg(&lt[k]), b = __ldg(&lx[i]), d = __ldg(&ly[j]);
+      const double lr = dv.psi * ((double)a.x - (double)b.x - (double)d.x);
+      const double li = dv.psi * ((double)a.y - (double)b.y - (double)d.y);
+      const double mag = lr * lr + li * li;
+      const double sigma = dv.adjoint ? mag : dv.m1 + mag * dv.inv_m2;
+      const R s = (R)(dv.inv_N / sigma);
+      buf[e] = cscale(buf[e], s);
+    }
+    __syncthreads();
+    smem_fft<R, kPEPT>(buf, lines, n, pl, twn, true);
+  }
+  for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+    const int a = e / lines, l = e - a * lines;
+    const long long q = l0 + l;
+    if (q >= total) continue;
+    const long long o = q / n_inner, c = q - o * n_inner;
+    spec[o * outer_stride + c + a * axis_stride] = buf[l * n + a];
+  }
+}
+
+template <typename R>
+cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const R* r, R* z, cplx<R>* spec,
+                          cudaStream_t st) {
+  using C = cplx<R>;
+  const Axis& At = P->ax[0];
+  const Axis& Ax = P->ax[1];
+  const Axis& Ay = P->ax[2];
+  const long long nrows = (long long)P->nt * P->nx;
+  const int ny = P->ny, H = P->H, Hp = P->Hp;
+  cudaError_t err;
+  // 1. rows forward
+  {
+    const int threads = (ny > kPEPT * 256) ? 512 : 256;
+    int pairs = (kPEPT * threads) / ny;
+    if (pairs < 1) pairs = 1;
+    const long long np = (nrows + 1) / 2;
+    if (pairs > np) pairs = (int)np;
+    const long long grid = (np + pairs - 1) / pairs;
+    k_prec_rows_fwd<R><<<(unsigned)grid, threads, (size_t)pairs * ny * sizeof(C), st>>>(
+        r, spec, nrows, ny, H, Hp, ptables<R>(Ay).twn, Ay.plann, pairs);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  const int threads = sizeof(R) == 4 ? 1024 : 512;
+  const int cap = kPEPT * threads;
+  DivArgs none{};
+  // 2. x1 forward; 3. t forward/divide/inverse; 4. x1 inverse
+  for (int step = 0; step < 3; ++step) {
+    const bool tpass = (step == 1);
+    const Axis& A = tpass ? At : Ax;
+    const int n = A.n;
+    long long axis_stride, n_inner, outer_stride, n_outer;
+    if (!tpass) {
+      axis_stride = Hp;
+      n_inner = H;
+      outer_stride = (long long)P->nx * Hp;
+      n_outer = P->nt;
+    } else {
+      axis_stride = (long long)P->nx * Hp;
+      n_inner = axis_stride;
+      outer_stride = 0;
+      n_outer = 1;
+    }
+    int lines = cap / n;
+    if (lines < 1) lines = 1;
+    const long long total = n_outer * n_inner;
+    if (lines > total) lines = (int)total;
+    const long long grid = (total + lines - 1) / lines;
+    DivArgs dv = none;
+    if (tpass) {
+      dv.divide = 1;
+      dv.adjoint = mode;
+      dv.m1 = m1;
+      dv.inv_m2 = 1.0 / m2;
+      dv.psi = P->psi;
+      dv.inv_N = 1.0 / (double)P->N;
+      dv.Hp = Hp;
+      dv.H = H;
+    }
+    k_prec_axis<R><<<(unsigned)grid, threads, (size_t)lines * n * sizeof(C), st>>>(
+        spec, n, axis_stride, n_inner, outer_stride, n_outer, ptables<R>(A).twn, A.plann, step == 2 ? 1 : 0, lines,
+        dv, ptables<R>(At).lam, ptables<R>(Ax).lam, ptables<R>(Ay).lam);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  // 5. rows inverse
+  {
+    const int threads2 = (ny > kPEPT * 256) ? 512 : 256;
+    int pairs = (kPEPT * threads2) / ny;
+    if (pairs < 1) pairs = 1;
+    const long long np = (nrows + 1) / 2;
+    if (pairs > np) pairs = (int)np;
+    const long long grid = (np + pairs - 1) / pairs;
+    k_prec_rows_inv<R><<<(unsigned)grid, threads2, (size_t)pairs * ny * sizeof(C), st>>>(
+        spec, z, nrows, ny, H, Hp, ptables<R>(Ay).twn, Ay.plann, pairs);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
+template cudaError_t apply_precond<double>(fde_problem*, double, double, int, const double*, double*, double2*,
+                                           cudaStream_t);
+template cudaError_t apply_precond<float>(fde_problem*, double, double, int, const float*, float*, float2*,
+                                          cudaStream_t);
+
+// Dynamic shared memory above 48 KB must be opted into per kernel.
+cudaError_t precond_set_smem_attrs() {
+  const int big = 200 * 1024;
+  cudaError_t e = cudaSuccess;
+  e = cudaFuncSetAttribute(k_prec_rows_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e) return e;
+  e = cudaFuncSetAttribute(k_prec_rows_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e) return e;
+  e = cudaFuncSetAttribute(k_prec_rows_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e) return e;
+  e = cudaFuncSetAttribute(k_prec_rows_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e) return e;
+  e = cudaFuncSetAttribute(k_prec_axis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e) return e;
+  return cudaFuncSetAttribute(k_prec_axis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
+}  // namespace fde

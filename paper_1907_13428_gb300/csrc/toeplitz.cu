@@ -1,0 +1,304 @@
+// Matrix-free products with the three-level Toeplitz operator
+//   B = psi (C_t (x) I - I (x) X (x) I - I (x) I (x) Y)
+// (Eq. FDE constraint matrix scaled by psi, Section 5) and with B^T.
+//
+// Each one-dimensional Toeplitz factor T (n x n) is applied by circulant
+// embedding (Table "Complexity table", Toeplitz row): with L the smallest power
+// of two >= n, T sits in a circulant of order 2L whose symbol lambda is the
+// DFT of the embedded first column. The order-2L transform is split into its
+// even and odd frequencies, which are two order-L transforms of x and of
+// x_j W_{2L}^j, so lines never need 2L storage:
+//   (T x)_i = 1/2 sum_{s=0,1} W_{2L}^{-s i} IFFT_L(lambda_{2k+s} FFT_L(x_j W_{2L}^{s j}))_i.
+// Real lines are processed two at a time as the real and imaginary parts of
+// one complex line (the product of a real line with a real circulant stays
+// real, so the two results separate exactly). The symbol halves are stored
+// pre-multiplied by coef/(2L), so a pass writes -psi X x (space) or +psi C_t x
+// (time) directly; B^T uses the conjugate symbol.
+//
+// Passes: the x2 axis (contiguous rows), then the x1 axis (columns of stride
+// ny). For alpha_t = 1 the time term (psi/h_t)(x_t - x_{t-1}) (reversed for
+// B^T) is folded into the x1 pass; for alpha_t < 1 a third pass applies the
+// lower-triangular Toeplitz C_t along t (stride nx*ny) by the same embedding.
+#include "internal.h"
+
+namespace fde {
+
+constexpr int kEPT = 16;  // complex elements staged per thread in an FFT pass
+
+// ---------------------------------------------------------------------------
+// x2 axis: rows of n contiguous values; a CTA takes `pairs` row pairs and
+// builds 2*pairs complex lines of length L (pair p, half s -> line 2p+s).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(512) k_rows(const R* __restrict__ x, R* __restrict__ out, long long nrows,
+                                               int n, int L, const cplx<R>* __restrict__ sym,
+                                               const cplx<R>* __restrict__ tw2, const cplx<R>* __restrict__ twL,
+                                               FftPlan pl, int conj_sym, int pairs) {
+  using C = cplx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const long long row0 = (long long)blockIdx.x * pairs * 2;
+  const int nl = 2 * pairs;
+  for (int e = threadIdx.x; e < pairs * L; e += blockDim.x) {
+    const int p = e / L, j = e - p * L;
+    const long long ra = row0 + 2 * p, rb = ra + 1;
+    R a = 0, b = 0;
+    if (j < n) {
+      if (ra < nrows) a = x[ra * n + j];
+      if (rb < nrows) b = x[rb * n + j];
+    }
+    const C v = mk<C>(a, b);
+    buf[(2 * p) * L + j] = v;
+    buf[(2 * p + 1) * L + j] = (j < n) ? cmul(v, __ldg(&tw2[j])) : mk<C>(0, 0);
+  }
+  __syncthreads();
+  smem_fft<R, kEPT>(buf, nl, L, pl, twL, false);
+  for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
+    const int l = e / L, k = e - l * L;
+    C w = __ldg(&sym[(l & 1) * L + k]);
+    if (conj_sym) w.y = -w.y;
+    buf[e] = cmul(buf[e], w);
+  }
+  __syncthreads();
+  smem_fft<R, kEPT>(buf, nl, L, pl, twL, true);
+  for (int e = threadIdx.x; e < pairs * n; e += blockDim.x) {
+    const int p = e / n, j = e - p * n;
+    const long long ra = row0 + 2 * p, rb = ra + 1;
+    const C v = cadd(buf[(2 * p) * L + j], cmul(buf[(2 * p + 1) * L + j], cconj(__ldg(&tw2[j]))));
+    if (ra < nrows) out[ra * n + j] = v.x;
+    if (rb < nrows) out[rb * n + j] = v.y;
+  }
+}
+
+// Epilogue of a strided-axis pass, per output element idx on time slice t:
+//   out = dsc(t) * (acc[idx] + res + ct * (xt[idx] - xt[idx -/+ plane])) + addc(t) * addv[idx]
+// with dsc/addc taking v0 on slices 0..nt-2 and v1 on the last slice.
+template <typename R> struct AxisEpi {
+  R* out;
+  const R* acc;   // nullable
+  const R* xt;    // nullable: time-difference term source
+  int tdir;       // +1: x_t - x_{t-1} (B), -1: x_t - x_{t+1} (B^T)
+  R ct;           // psi / h_t
+  long long plane;
+  int nt;
+  int t_is_axis;  // 1: time index = position along the axis; 0: = outer index
+  int has_dsc;
+  R dsc0, dsc1;
+  const R* addv;  // nullable
+  R addc0, addc1;
+};
+
+template <typename R>
+__device__ __forceinline__ void axis_store(const AxisEpi<R>& E, long long idx, int t, R res) {
+  R v = res;
+  if (E.acc) v += E.acc[idx];
+  if (E.xt) {
+    R nb = 0;
+    if (E.tdir > 0) {
+      if (t > 0) nb = E.xt[idx - E.plane];
+    } else {
+      if (t < E.nt - 1) nb = E.xt[idx + E.plane];
+    }
+    v += E.ct * (E.xt[idx] - nb);
+  }
+  const bool last = (t == E.nt - 1);
+  if (E.has_dsc) v *= last ? E.dsc1 : E.dsc0;
+  if (E.addv) v += (last ? E.addc1 : E.addc0) * E.addv[idx];
+  E.out[idx] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Strided axis: line (o, c) reads x[o*outer_stride + c + a*axis_stride],
+// a in [0, n); inner indices c are taken in pairs (c, c+1) packed as one
+// complex line. A CTA takes `pairs` consecutive pairs (inner fastest).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(1024) k_axis(const R* __restrict__ x, int n, int L, long long axis_stride,
+                                                long long n_inner, long long outer_stride, long long n_outer,
+                                                const cplx<R>* __restrict__ sym, const cplx<R>* __restrict__ tw2,
+                                                const cplx<R>* __restrict__ twL, FftPlan pl, int conj_sym,
+                                                int pairs, AxisEpi<R> E) {
+  using C = cplx<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const long long npi = (n_inner + 1) / 2;
+  const long long total = n_outer * npi;
+  const long long q0 = (long long)blockIdx.x * pairs;
+  const int nl = 2 * pairs;
+  for (int e = threadIdx.x; e < pairs * L; e += blockDim.x) {
+    const int a = e / pairs, p = e - a * pairs;
+    const long long q = q0 + p;
+    R va = 0, vb = 0;
+    if (q < total && a < n) {
+      const long long o = q / npi, c = 2 * (q - o * npi);
+      const long long idx = o * outer_stride + c + a * axis_stride;
+      va = x[idx];
+      if (c + 1 < n_inner) vb = x[idx + 1];
+    }
+    const C v = mk<C>(va, vb);
+    buf[(2 * p) * L + a] = v;
+    buf[(2 * p + 1) * L + a] = (a < n) ? cmul(v, __ldg(&tw2[a])) : mk<C>(0, 0);
+  }
+  __syncthreads();
+  smem_fft<R, kEPT>(buf, nl, L, pl, twL, false);
+  for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
+    const int l = e / L, k = e - l * L;
+    C w = __ldg(&sym[(l & 1) * L + k]);
+    if (conj_sym) w.y = -w.y;
+    buf[e] = cmul(buf[e], w);
+  }
+  __syncthreads();
+  smem_fft<R, kEPT>(buf, nl, L, pl, twL, true);
+  for (int e = threadIdx.x; e < pairs * n; e += blockDim.x) {
+    const int a = e / pairs, p = e - a * pairs;
+    const long long q = q0 + p;
+    if (q >= total) continue;
+    const long long o = q / npi, c = 2 * (q - o * npi);
+    const long long idx = o * outer_stride + c + a * axis_stride;
+    const C v = cadd(buf[(2 * p) * L + a], cmul(buf[(2 * p + 1) * L + a], cconj(__ldg(&tw2[a]))));
+    const int t = E.t_is_axis ? a : (int)o;
+    axis_store(E, idx, t, v.x);
+    if (c + 1 < n_inner) axis_store(E, idx + 1, t, v.y);
+  }
+}
+
+template <typename R> static const AxisTables<R>& tables(const Axis& A);
+template <> const AxisTables<double>& tables<double>(const Axis& A) { return A.d; }
+template <> const AxisTables<float>& tables<float>(const Axis& A) { return A.f; }
+
+template <typename R> static int rows_threads(int L) { return (2 * L > kEPT * 256) ? 512 : 256; }
+
+template <typename R>
+static cudaError_t launch_rows(fde_problem* P, const R* x, R* out, int conj_sym, const cplx<R>* sym,
+                               cudaStream_t st) {
+  const Axis& A = P->ax[2];
+  const AxisTables<R>& T = tables<R>(A);
+  const int L = A.L;
+  const int threads = rows_threads<R>(L);
+  const int cap = kEPT * threads;  // complex elements per CTA
+  int pairs = cap / (2 * L);
+  if (pairs < 1) pairs = 1;
+  const long long nrows = (long long)P->nt * P->nx;
+  const long long npairs = (nrows + 1) / 2;
+  if (pairs > npairs) pairs = (int)npairs;
+  const long long grid = (npairs + pairs - 1) / pairs;
+  const size_t smem = (size_t)2 * pairs * L * sizeof(cplx<R>);
+  k_rows<R><<<(unsigned)grid, threads, smem, st>>>(x, out, nrows, A.n, L, sym ? sym : T.sym, T.tw2, T.twL,
+                                                   A.planL, conj_sym, pairs);
+  return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t launch_axis(fde_problem* P, int axis, const R* x, int conj_sym, const cplx<R>* sym,
+                               const AxisEpi<R>& E, cudaStream_t st) {
+  const Axis& A = P->ax[axis];
+  const AxisTables<R>& T = tables<R>(A);
+  const int L = A.L;
+  const int threads = sizeof(R) == 4 ? 1024 : 512;
+  const int cap = kEPT * threads;
+  int pairs = cap / (2 * L);
+  if (pairs < 1) pairs = 1;
+  long long axis_stride, n_inner, outer_stride, n_outer;
+  if (axis == 1) {  // x1: lines along x1 inside each time slice
+    axis_stride = P->ny;
+    n_inner = P->ny;
+    outer_stride = (long long)P->nx * P->ny;
+    n_outer = P->nt;
+  } else {  // time: lines along t
+    axis_stride = (long long)P->nx * P->ny;
+    n_inner = axis_stride;
+    outer_stride = 0;
+    n_outer = 1;
+  }
+  const long long total = n_outer * ((n_inner + 1) / 2);
+  if (pairs > total) pairs = (int)total;
+  const long long grid = (total + pairs - 1) / pairs;
+  const size_t smem = (size_t)2 * pairs * L * sizeof(cplx<R>);
+  k_axis<R><<<(unsigned)grid, threads, smem, st>>>(x, A.n, L, axis_stride, n_inner, outer_stride, n_outer,
+                                                   sym ? sym : T.sym, T.tw2, T.twL, A.planL, conj_sym, pairs, E);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t apply_B(fde_problem* P, int transpose, const R* x, R* y, const SliceDiag* dscale, const R* addv,
+                    const SliceDiag* addc, R* tmp1, R* tmp2, cudaStream_t st) {
+  cudaError_t err = launch_rows<R>(P, x, tmp1, transpose, nullptr, st);
+  if (err != cudaSuccess) return err;
+  const R* acc = tmp1;
+  if (!P->euler) {
+    AxisEpi<R> Et{};
+    Et.out = tmp2;
+    Et.acc = tmp1;
+    Et.nt = P->nt;
+    Et.t_is_axis = 1;
+    err = launch_axis<R>(P, 0, x, transpose, nullptr, Et, st);
+    if (err != cudaSuccess) return err;
+    acc = tmp2;
+  }
+  AxisEpi<R> E{};
+  E.out = y;
+  E.acc = acc;
+  E.nt = P->nt;
+  E.plane = (long long)P->nx * P->ny;
+  E.t_is_axis = 0;
+  if (P->euler) {
+    E.xt = x;
+    E.tdir = transpose ? -1 : 1;
+    E.ct = (R)(P->psi / P->ht);
+  }
+  if (dscale) {
+    E.has_dsc = 1;
+    E.dsc0 = (R)dscale->v[0];
+    E.dsc1 = (R)dscale->v[1];
+  }
+  if (addv) {
+    E.addv = addv;
+    E.addc0 = (R)addc->v[0];
+    E.addc1 = (R)addc->v[1];
+  }
+  return launch_axis<R>(P, 1, x, transpose, nullptr, E, st);
+}
+
+template <typename R>
+cudaError_t apply_S(fde_problem* P, const SliceDiag& M1, const SliceDiag& M2inv, const R* x, R* y, R* w, R* tmp1,
+                    R* tmp2, cudaStream_t st) {
+  cudaError_t err = apply_B<R>(P, 0, x, w, &M2inv, nullptr, nullptr, tmp1, tmp2, st);
+  if (err != cudaSuccess) return err;
+  return apply_B<R>(P, 1, w, y, nullptr, x, &M1, tmp1, tmp2, st);
+}
+
+template <typename R>
+cudaError_t apply_axis_raw(fde_problem* P, int axis, const R* x, R* y, const cplx<R>* sym, int conj_sym,
+                           cudaStream_t st) {
+  // one spatial factor along one axis (no time term, no accumulation)
+  if (axis == 2) return launch_rows<R>(P, x, y, conj_sym, sym, st);
+  AxisEpi<R> E{};
+  E.out = y;
+  E.nt = P->nt;
+  E.plane = (long long)P->nx * P->ny;
+  return launch_axis<R>(P, axis, x, conj_sym, sym, E, st);
+}
+
+template cudaError_t apply_B<double>(fde_problem*, int, const double*, double*, const SliceDiag*, const double*,
+                                     const SliceDiag*, double*, double*, cudaStream_t);
+template cudaError_t apply_B<float>(fde_problem*, int, const float*, float*, const SliceDiag*, const float*,
+                                    const SliceDiag*, float*, float*, cudaStream_t);
+template cudaError_t apply_S<double>(fde_problem*, const SliceDiag&, const SliceDiag&, const double*, double*,
+                                     double*, double*, double*, cudaStream_t);
+template cudaError_t apply_S<float>(fde_problem*, const SliceDiag&, const SliceDiag&, const float*, float*, float*,
+                                    float*, float*, cudaStream_t);
+template cudaError_t apply_axis_raw<double>(fde_problem*, int, const double*, double*, const double2*, int,
+                                            cudaStream_t);
+
+}  // namespace fde
+
+namespace fde {
+cudaError_t toeplitz_set_smem_attrs() {
+  const int big = 200 * 1024;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_axis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  return cudaFuncSetAttribute(k_axis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+}  // namespace fde

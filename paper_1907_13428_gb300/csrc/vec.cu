@@ -1,0 +1,363 @@
+// Streaming vector kernels: deterministic reductions (fixed grid, per-block
+// tree, then a one-block fixed-order tree), the fused PCG updates, the
+// refinement conversions and the ADMM clip-and-update step (Algorithm 1 steps
+// for z, p and w with the psi scaling of Section 6.1).
+#include <cmath>
+
+#include "internal.h"
+#include "vec.h"
+
+namespace fde {
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  return v;  // valid in thread 0
+}
+
+__device__ __forceinline__ double block_max(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  __syncthreads();
+  return v;
+}
+
+int red_grid(long long n) {
+  long long g = (n + 4LL * kRedThreads - 1) / (4LL * kRedThreads);
+  if (g < 1) g = 1;
+  if (g > kMaxPartials) g = kMaxPartials;
+  return (int)g;
+}
+
+// partials[b] = sum over the grid-stride share of block b of a[i]*b[i]
+template <typename RA, typename RB>
+__global__ void __launch_bounds__(kRedThreads) k_dot(const RA* __restrict__ a, const RB* __restrict__ b, long long n,
+                                                      double* __restrict__ partials) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s += (double)a[i] * (double)b[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// Sum the partials in a fixed order and derive PCG scalars.
+//   op FIN_STORE: dscal[slot] = sum
+//   op FIN_ALPHA: dscal[S_PQ] = sum; alpha = rz / sum (flag breakdown if sum <= 0)
+//   op FIN_BETA : beta = sum / rz; rz = sum
+__global__ void __launch_bounds__(1024) k_finish(const double* __restrict__ partials, int np, double* dscal, int slot,
+                                                  int op) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += partials[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    if (!isfinite(s)) dscal[S_FLAG] = (double)FDE_ENONFINITE;
+    if (op == FIN_STORE) {
+      dscal[slot] = s;
+    } else if (op == FIN_ALPHA) {
+      dscal[S_PQ] = s;
+      if (!(s > 0.0)) {
+        dscal[S_FLAG] = (double)FDE_EBREAKDOWN;
+        dscal[S_ALPHA] = 0.0;
+      } else {
+        dscal[S_ALPHA] = dscal[S_RZ] / s;
+      }
+    } else if (op == FIN_BETA) {
+      const double rz = dscal[S_RZ];
+      dscal[S_BETA] = rz != 0.0 ? s / rz : 0.0;
+      dscal[S_RZ] = s;
+    } else if (op == FIN_RZ0) {
+      dscal[S_RZ] = s;
+    }
+  }
+}
+
+// x += alpha d; r -= alpha q; partials of r.r
+template <typename RV>
+__global__ void __launch_bounds__(kRedThreads) k_pcg_xr(RV* __restrict__ x, RV* __restrict__ r, const RV* __restrict__ d,
+                                                         const RV* __restrict__ q, const double* __restrict__ dscal,
+                                                         long long n, double* __restrict__ partials) {
+  __shared__ double sh[32];
+  const double alpha = dscal[S_ALPHA];
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    x[i] = (RV)((double)x[i] + alpha * (double)d[i]);
+    const RV ri = (RV)((double)r[i] - alpha * (double)q[i]);
+    r[i] = ri;
+    s += (double)ri * (double)ri;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// d = z + beta d
+template <typename RV>
+__global__ void k_pcg_p(RV* __restrict__ d, const RV* __restrict__ z, const double* __restrict__ dscal, long long n) {
+  const double beta = dscal[S_BETA];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    d[i] = (RV)((double)z[i] + beta * (double)d[i]);
+}
+
+// r = b - s (double); partials of r.r
+__global__ void __launch_bounds__(kRedThreads) k_residual(const double* __restrict__ b, const double* __restrict__ s,
+                                                           double* __restrict__ r, long long n,
+                                                           double* __restrict__ partials) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = b[i] - s[i];
+    r[i] = v;
+    acc += v * v;
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+// out32 = (float) in64
+__global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+// y64 += (double) d32
+__global__ void k_add_f32(double* __restrict__ y, const float* __restrict__ d, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += (double)d[i];
+}
+
+template <typename R>
+__global__ void k_fill(R* __restrict__ x, R v, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+template <typename R>
+__global__ void k_copy(R* __restrict__ dst, const R* __restrict__ src, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+// ---------------------------------------------------------------------------
+// ADMM (Algorithm 1, psi-scaled, sub-problem merged with the p update).
+// Slice-constant diagonals (index 0: slices 0..nt-2, 1: last slice):
+//   M1 = rho (w + 1/delta), Q = rho (gamma w + psi^2/delta), M2 = psi^2/Q + delta/rho.
+// Pre-step, from (z_y, z_u, p, w_y, w_u):
+//   c   = rho (w ybar - w_y + z_y/delta)
+//   b_u = rho (-psi w_u + psi^2 z_u/delta) + (1-rho) psi p
+//   r0  = psi b_u / Q - psi g + (delta/rho) p
+//   q   = (1-rho) p - r0 / M2
+// and then rhs = c + B^T q is the right-hand side of S y = rhs.
+// ---------------------------------------------------------------------------
+__global__ void k_admm_pre(const AdmmArgs A, double* __restrict__ c, double* __restrict__ bu, double* __restrict__ r0,
+                           double* __restrict__ q) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.n; i += (long long)gridDim.x * blockDim.x) {
+    const int last = (i >= A.last_start);
+    const double w = A.w[last], Q = A.Q[last], M2 = A.M2[last];
+    const double p = A.p[i];
+    const double gi = A.g ? A.g[i] : 0.0;
+    c[i] = A.rho * (w * A.ybar[i] - A.wy[i] + A.zy[i] * A.inv_delta);
+    const double b = A.rho * (-A.psi * A.wu[i] + A.psi * A.psi * A.zu[i] * A.inv_delta) + (1.0 - A.rho) * A.psi * p;
+    bu[i] = b;
+    const double r = A.psi * b / Q - A.psi * gi + A.delta_over_rho * p;
+    r0[i] = r;
+    q[i] = (1.0 - A.rho) * p - r / M2;
+  }
+}
+
+// Post-step, given y and By:
+//   p   = (By + r0) / M2,  u = (b_u - psi p) / Q,
+//   z_y = clip(y + delta w_y, ya, yb),  z_u = clip(u + delta w_u / psi, ua, ub),
+//   w_y += (rho/delta)(y - z_y),  w_u += (rho/delta) psi (u - z_u),
+// and block maxima of |By + psi (u - g)|, |y - z_y|, |u - z_u| plus block sums
+// of the objective terms w (y - ybar)^2 and gamma w u^2.
+__global__ void __launch_bounds__(kRedThreads) k_admm_post(const AdmmArgs A, const double* __restrict__ y,
+                                                            const double* __restrict__ By,
+                                                            const double* __restrict__ bu,
+                                                            const double* __restrict__ r0, double* __restrict__ u,
+                                                            double* __restrict__ partials, int np) {
+  __shared__ double sh[32];
+  double m_eq = 0.0, m_y = 0.0, m_u = 0.0, obj = 0.0;
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.n; i += (long long)gridDim.x * blockDim.x) {
+    const int last = (i >= A.last_start);
+    const double w = A.w[last], Q = A.Q[last], M2 = A.M2[last];
+    const double yi = y[i], byi = By[i];
+    const double p = (byi + r0[i]) / M2;
+    const double ui = (bu[i] - A.psi * p) / Q;
+    const double lo_y = A.ya ? A.ya[i] : A.ya_s, hi_y = A.yb ? A.yb[i] : A.yb_s;
+    const double lo_u = A.ua ? A.ua[i] : A.ua_s, hi_u = A.ub ? A.ub[i] : A.ub_s;
+    const double zy = fmin(fmax(yi + A.delta * A.wy[i], lo_y), hi_y);
+    const double zu = fmin(fmax(ui + A.delta * A.wu[i] / A.psi, lo_u), hi_u);
+    A.wy[i] += A.rho_over_delta * (yi - zy);
+    A.wu[i] += A.rho_over_delta * A.psi * (ui - zu);
+    A.zy[i] = zy;
+    A.zu[i] = zu;
+    A.p[i] = p;
+    u[i] = ui;
+    const double gi = A.g ? A.g[i] : 0.0;
+    const double e = fabs(byi + A.psi * (ui - gi));
+    const double dy = fabs(yi - zy), du = fabs(ui - zu);
+    bad |= !isfinite(e) || !isfinite(dy) || !isfinite(du);
+    m_eq = fmax(m_eq, e);
+    m_y = fmax(m_y, dy);
+    m_u = fmax(m_u, du);
+    const double dd = yi - A.ybar[i];
+    obj += 0.5 * w * dd * dd + 0.5 * A.gamma * w * ui * ui;
+  }
+  m_eq = block_max(m_eq, sh);
+  m_y = block_max(m_y, sh);
+  m_u = block_max(m_u, sh);
+  obj = block_sum(obj, sh);
+  const double flag = block_max(bad ? 1.0 : 0.0, sh);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = m_eq;
+    partials[np + blockIdx.x] = m_y;
+    partials[2 * np + blockIdx.x] = m_u;
+    partials[3 * np + blockIdx.x] = obj;
+    partials[4 * np + blockIdx.x] = flag;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_admm_finish(const double* __restrict__ partials, int np, double* dscal) {
+  __shared__ double sh[32];
+  double a = 0.0, b = 0.0, c = 0.0, o = 0.0, f = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    a = fmax(a, partials[i]);
+    b = fmax(b, partials[np + i]);
+    c = fmax(c, partials[2 * np + i]);
+    o += partials[3 * np + i];
+    f = fmax(f, partials[4 * np + i]);
+  }
+  a = block_max(a, sh);
+  b = block_max(b, sh);
+  c = block_max(c, sh);
+  o = block_sum(o, sh);
+  f = block_max(f, sh);
+  if (threadIdx.x == 0) {
+    dscal[S_RES_EQ] = a;
+    dscal[S_RES_Y] = b;
+    dscal[S_RES_U] = c;
+    dscal[S_OBJ] = o;
+    if (f > 0.0) dscal[S_FLAG] = (double)FDE_ENONFINITE;
+  }
+}
+
+// dJ/dybar = -w (y - ybar); rhs of the adjoint: f = -w (y - ybar) - w_y
+__global__ void k_grad_ybar(const double* __restrict__ y, const double* __restrict__ ybar, const double* __restrict__ wy,
+                            double w0, double w1, long long last_start, long long n, double* __restrict__ dJ,
+                            double* __restrict__ f) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double w = i >= last_start ? w1 : w0;
+    const double v = -w * (y[i] - ybar[i]);
+    if (dJ) dJ[i] = v;
+    f[i] = v - (wy ? wy[i] : 0.0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static unsigned sgrid(long long n) {
+  long long g = (n + 255) / 256;
+  if (g > 152LL * 16) g = 152LL * 16;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+template <typename RA, typename RB>
+cudaError_t dot(fde_problem* P, const RA* a, const RB* b, long long n, int slot, int op, cudaStream_t st) {
+  const int g = red_grid(n);
+  k_dot<RA, RB><<<g, kRedThreads, 0, st>>>(a, b, n, P->partials);
+  k_finish<<<1, 1024, 0, st>>>(P->partials, g, P->dscal, slot, op);
+  return cudaGetLastError();
+}
+template cudaError_t dot<double, double>(fde_problem*, const double*, const double*, long long, int, int, cudaStream_t);
+template cudaError_t dot<float, float>(fde_problem*, const float*, const float*, long long, int, int, cudaStream_t);
+
+template <typename RV>
+cudaError_t pcg_xr(fde_problem* P, RV* x, RV* r, const RV* d, const RV* q, long long n, cudaStream_t st) {
+  const int g = red_grid(n);
+  k_pcg_xr<RV><<<g, kRedThreads, 0, st>>>(x, r, d, q, P->dscal, n, P->partials);
+  k_finish<<<1, 1024, 0, st>>>(P->partials, g, P->dscal, S_RR, FIN_STORE);
+  return cudaGetLastError();
+}
+template cudaError_t pcg_xr<double>(fde_problem*, double*, double*, const double*, const double*, long long,
+                                    cudaStream_t);
+template cudaError_t pcg_xr<float>(fde_problem*, float*, float*, const float*, const float*, long long, cudaStream_t);
+
+template <typename RV>
+cudaError_t pcg_p(fde_problem* P, RV* d, const RV* z, long long n, cudaStream_t st) {
+  k_pcg_p<RV><<<sgrid(n), 256, 0, st>>>(d, z, P->dscal, n);
+  return cudaGetLastError();
+}
+template cudaError_t pcg_p<double>(fde_problem*, double*, const double*, long long, cudaStream_t);
+template cudaError_t pcg_p<float>(fde_problem*, float*, const float*, long long, cudaStream_t);
+
+cudaError_t residual(fde_problem* P, const double* b, const double* s, double* r, long long n, int slot,
+                     cudaStream_t st) {
+  const int g = red_grid(n);
+  k_residual<<<g, kRedThreads, 0, st>>>(b, s, r, n, P->partials);
+  k_finish<<<1, 1024, 0, st>>>(P->partials, g, P->dscal, slot, FIN_STORE);
+  return cudaGetLastError();
+}
+
+cudaError_t to_f32(const double* in, float* out, long long n, cudaStream_t st) {
+  k_to_f32<<<sgrid(n), 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+cudaError_t add_f32(double* y, const float* d, long long n, cudaStream_t st) {
+  k_add_f32<<<sgrid(n), 256, 0, st>>>(y, d, n);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t fill(R* x, R v, long long n, cudaStream_t st) {
+  k_fill<R><<<sgrid(n), 256, 0, st>>>(x, v, n);
+  return cudaGetLastError();
+}
+template cudaError_t fill<double>(double*, double, long long, cudaStream_t);
+template cudaError_t fill<float>(float*, float, long long, cudaStream_t);
+template <typename R>
+cudaError_t copy(R* dst, const R* src, long long n, cudaStream_t st) {
+  k_copy<R><<<sgrid(n), 256, 0, st>>>(dst, src, n);
+  return cudaGetLastError();
+}
+template cudaError_t copy<double>(double*, const double*, long long, cudaStream_t);
+template cudaError_t copy<float>(float*, const float*, long long, cudaStream_t);
+
+cudaError_t admm_pre(const AdmmArgs& A, double* c, double* bu, double* r0, double* q, cudaStream_t st) {
+  k_admm_pre<<<sgrid(A.n), 256, 0, st>>>(A, c, bu, r0, q);
+  return cudaGetLastError();
+}
+
+cudaError_t admm_post(fde_problem* P, const AdmmArgs& A, const double* y, const double* By, const double* bu,
+                      const double* r0, double* u, cudaStream_t st) {
+  int g = red_grid(A.n);
+  if (g > kMaxPartials / 5) g = kMaxPartials / 5;
+  k_admm_post<<<g, kRedThreads, 0, st>>>(A, y, By, bu, r0, u, P->partials, g);
+  k_admm_finish<<<1, 1024, 0, st>>>(P->partials, g, P->dscal);
+  return cudaGetLastError();
+}
+
+cudaError_t grad_ybar(const double* y, const double* ybar, const double* wy, double w0, double w1, long long last_start,
+                      long long n, double* dJ, double* f, cudaStream_t st) {
+  k_grad_ybar<<<sgrid(n), 256, 0, st>>>(y, ybar, wy, w0, w1, last_start, n, dJ, f);
+  return cudaGetLastError();
+}
+
+}  // namespace fde

@@ -1,0 +1,161 @@
+"""GPU parity of the ADMM solve (Algorithm 1) and of the gradient against the
+FP64 oracle, through the C ABI.
+
+Tolerances (relative, infinity norm): FP64 1e-10 and MIXED 1e-8, the targets
+of the workload specification. Fixed-iteration comparisons use exact oracle
+sub-solves against GPU sub-solves converged to 1e-13 (FP64) or refined to
+1e-12 (MIXED), so the only differences are rounding and the sub-solve
+residual, amplified by at most the condition number of S (< 1e3 here)."""
+import numpy as np
+import pytest
+import torch
+
+import fde_inputs as fi
+import oracle as O
+from gpu_util import dev, host, lib, need_gpu, params, relerr
+
+pytestmark = pytest.mark.gpu
+
+
+def _instance(nx, ny, nt, seed=3, **boxes):
+    p = params(nx, ny, nt, gamma=1e-3)
+    ybar = fi.desired_state_sine(p, seed)
+    g = 0.05 * fi.random_field(seed + 11, (nt, nx, ny))
+    return fi.FdeInstance(p, ybar, g, boxes.get("ya"), boxes.get("yb"), boxes.get("ua"), boxes.get("ub"), seed)
+
+
+def _run(F, inst, opts):
+    prob = F.Problem(inst.params)
+    r = prob.admm_solve(opts, dev(inst.ybar), g=None if inst.g is None else dev(inst.g), ya=inst.ya, yb=inst.yb,
+                        ua=inst.ua, ub=inst.ub, allow_noconv=True)
+    prob.close()
+    return r
+
+
+BOXES = [dict(ua=-0.05, ub=0.05), dict(yb=0.3), dict(ya=-0.1, yb=0.25, ua=-0.2, ub=0.1), dict()]
+
+
+@pytest.mark.parametrize("boxes", BOXES)
+@pytest.mark.parametrize("dims", [(5, 4, 3), (8, 6, 5), (16, 16, 8)])
+def test_admm_fixed_iterations_fp64(dims, boxes):
+    need_gpu()
+    F = lib()
+    inst = _instance(*dims, **boxes)
+    K = 12
+    o = O.AdmmOptions(delta=0.8, rho=1.618)
+    ref = O.admm_direct(inst, o, iters=K)
+    fo = F.AdmmOptions(delta=0.8, rho=1.618, max_admm=K, fixed_iters=True, inner_tol_mode=1, inner_tol=1e-13,
+                       precision=F.FDE_FP64)
+    r = _run(F, inst, fo)
+    assert r["stats"]["admm_iters"] == K
+    assert relerr(host(r["y"]), ref.y) < 1e-10
+    assert relerr(host(r["u"]), ref.u) < 1e-10
+    assert relerr(host(r["p"]), ref.p) < 1e-10
+    assert relerr(host(r["zu"]), ref.zu) < 1e-10
+    res = (r["stats"]["res_eq"], r["stats"]["res_y"], r["stats"]["res_u"])
+    assert np.allclose(res, ref.residuals, rtol=1e-6, atol=1e-12)
+
+
+@pytest.mark.parametrize("boxes", BOXES[:3])
+def test_admm_fixed_iterations_mixed(boxes):
+    need_gpu()
+    F = lib()
+    inst = _instance(16, 12, 6, **boxes)
+    K = 12
+    o = O.AdmmOptions(delta=0.8, rho=1.618)
+    ref = O.admm_direct(inst, o, iters=K)
+    fo = F.AdmmOptions(delta=0.8, rho=1.618, max_admm=K, fixed_iters=True, inner_tol_mode=1, inner_tol=1e-12,
+                       precision=F.FDE_MIXED, inner_tol_mixed=1e-4)
+    r = _run(F, inst, fo)
+    assert r["stats"]["refine_steps"] > 0
+    for k in ("y", "u", "p"):
+        assert relerr(host(r[k]), getattr(ref, k)) < 1e-8, k
+
+
+def test_admm_converged_matches_polished_kkt():
+    need_gpu()
+    F = lib()
+    inst = _instance(8, 6, 5, ua=-0.05, ub=0.05, yb=0.3)
+    o = O.AdmmOptions(delta=1.0, rho=1.618, tol=1e-11, max_iter=20000)
+    st = O.admm_direct(inst, o)
+    sol = O.polish(inst, st)
+    fo = F.AdmmOptions(delta=1.0, rho=1.618, tol_admm=1e-11, max_admm=20000, inner_tol_mode=1, inner_tol=1e-13)
+    r = _run(F, inst, fo)
+    assert r["status"] == F.FDE_OK
+    y, u = host(r["y"]), host(r["u"])
+    assert relerr(y, sol.y) < 1e-8 and relerr(u, sol.u) < 1e-8
+    # invariants: copies inside the box, residuals below tolerance
+    zu = host(r["zu"])
+    assert np.all(zu >= -0.05) and np.all(zu <= 0.05)
+    s = r["stats"]
+    assert max(s["res_eq"], s["res_y"], s["res_u"]) <= 1e-11
+    assert abs(s["objective"] - sol.J) <= 1e-8 * abs(sol.J)
+
+
+def test_admm_small_workload_fp64_and_mixed():
+    """32x32 x 16 workload (control box [-0.5, 0.5], tol 1e-6): GPU FP64 and MIXED
+    iterates after K iterations against the oracle's exact sub-solves."""
+    need_gpu()
+    F = lib()
+    inst = fi.config_small()
+    K = 6
+    o = O.AdmmOptions(delta=1.0, rho=1.618)
+    ref = O.admm_direct(inst, o, iters=K)
+    for prec, tol, inner in ((F.FDE_FP64, 1e-10, 1e-13), (F.FDE_MIXED, 1e-8, 1e-12)):
+        fo = F.AdmmOptions(delta=1.0, rho=1.618, max_admm=K, fixed_iters=True, inner_tol_mode=1, inner_tol=inner,
+                           precision=prec)
+        r = _run(F, inst, fo)
+        for k in ("y", "u", "p"):
+            assert relerr(host(r[k]), getattr(ref, k)) < tol, (prec, k, relerr(host(r[k]), getattr(ref, k)))
+
+
+def test_admm_small_workload_converges():
+    need_gpu()
+    F = lib()
+    inst = fi.config_small()
+    fo = F.AdmmOptions(delta=1.0, rho=1.618, tol_admm=1e-6, max_admm=2000, inner_tol_mode=0, precision=F.FDE_MIXED)
+    r = _run(F, inst, fo)
+    s = r["stats"]
+    assert r["status"] == F.FDE_OK, s
+    assert max(s["res_eq"], s["res_y"], s["res_u"]) <= 1e-6
+    zu = host(r["zu"])
+    assert zu.min() >= -0.5 and zu.max() <= 0.5
+
+
+def test_gradient_matches_oracle_and_closed_form():
+    need_gpu()
+    F = lib()
+    inst = _instance(6, 5, 4, ua=-0.05, ub=0.05)
+    inst.g = None
+    p = inst.params
+    o = O.AdmmOptions(delta=1.0, rho=1.618, tol=1e-11, max_iter=50000)
+    st = O.admm_direct(inst, o)
+    sol = O.polish(inst, st)
+    ref = O.objective_gradient(inst, sol)
+    prob = F.Problem(p)
+    dJ, coef, pv = prob.admm_grad(dev(sol.y), dev(inst.ybar), tol=1e-14)
+    assert relerr(host(dJ), ref["ybar"]) < 1e-12
+    assert relerr(host(pv), sol.p) < 1e-9
+    for i, k in enumerate(("dp", "dm", "ep", "em")):
+        assert abs(float(coef[i]) - ref[k]) <= 1e-9 * max(1.0, abs(ref[k])), (k, float(coef[i]), ref[k])
+    prob.close()
+
+
+def test_autograd_function_gradients():
+    need_gpu()
+    F = lib()
+    inst = _instance(6, 5, 4, ua=-0.05, ub=0.05)
+    inst.g = None
+    p = inst.params
+    ybar = dev(inst.ybar).view(p.nt, p.nx, p.ny).requires_grad_(True)
+    coef = torch.tensor([p.dp, p.dm, p.ep, p.em], dtype=torch.float64, requires_grad=True)
+    fo = F.AdmmOptions(delta=1.0, rho=1.618, tol_admm=1e-11, max_admm=50000, inner_tol_mode=1, inner_tol=1e-13)
+    J = F.solve_objective(ybar, coef, p, fo, dict(ua=-0.05, ub=0.05))
+    J.backward()
+    st = O.admm_direct(inst, O.AdmmOptions(delta=1.0, rho=1.618, tol=1e-11, max_iter=50000))
+    sol = O.polish(inst, st)
+    ref = O.objective_gradient(inst, sol)
+    assert abs(float(J) - sol.J) <= 1e-8 * abs(sol.J)
+    assert relerr(host(ybar.grad), ref["ybar"]) < 1e-7
+    for i, k in enumerate(("dp", "dm", "ep", "em")):
+        assert abs(float(coef.grad[i]) - ref[k]) <= 1e-6 * max(1.0, abs(ref[k]))

@@ -1,0 +1,141 @@
+"""GPU parity of the operator and preconditioner kernels against the FP64 oracle,
+through the C ABI. FP64 tolerance: 1e-12 relative (infinity norm) for products
+whose rounding error is a few hundred ulps; FP32: 2e-5 (float eps 6e-8 times
+the log-depth of the transforms and the operator's dynamic range)."""
+import numpy as np
+import pytest
+import torch
+
+import fde_inputs as fi
+import oracle as O
+from gpu_util import dev, host, lib, need_gpu, params, relerr
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(1, 1, 1), (2, 3, 1), (3, 5, 2), (5, 7, 4), (7, 8, 3), (8, 8, 8), (16, 12, 5), (33, 17, 6), (64, 64, 4),
+         (100, 50, 3)]
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.6])
+@pytest.mark.parametrize("dims", SIZES)
+def test_matvec_B_BT_fp64(dims, alpha):
+    need_gpu()
+    F = lib()
+    nx, ny, nt = dims
+    p = params(nx, ny, nt, alpha_t=alpha)
+    prob = F.Problem(p)
+    x = fi.random_field(17, (nt, nx, ny))
+    xd = dev(x)
+    for op, tr in ((F.FDE_OP_B, False), (F.FDE_OP_BT, True)):
+        got = host(prob.matvec(xd, op))
+        ref = O.apply_B(p, x, transpose=tr)
+        assert relerr(got, ref) < 1e-12, (op, relerr(got, ref))
+    prob.close()
+
+
+@pytest.mark.parametrize("dims", SIZES[:8])
+def test_matvec_S_fp64_and_fp32(dims):
+    need_gpu()
+    F = lib()
+    nx, ny, nt = dims
+    p = params(nx, ny, nt)
+    o = O.AdmmOptions(delta=0.7, rho=1.4)
+    prob = F.Problem(p)
+    x = fi.random_field(5, (nt, nx, ny))
+    fo = F.AdmmOptions(delta=0.7, rho=1.4)
+    got = host(prob.matvec(dev(x), F.FDE_OP_S, fo))
+    ref = O.apply_S(p, o, x)
+    assert relerr(got, ref) < 1e-12
+    got32 = host(prob.matvec(dev(x, torch.float32), F.FDE_OP_S, fo))
+    assert relerr(got32, ref) < 2e-5
+    for op, tr in ((F.FDE_OP_B, False), (F.FDE_OP_BT, True)):
+        g32 = host(prob.matvec(dev(x, torch.float32), op))
+        assert relerr(g32, O.apply_B(p, x, transpose=tr)) < 2e-5
+    prob.close()
+
+
+PSIZES = [(1, 1, 1), (2, 3, 1), (3, 5, 2), (5, 7, 4), (6, 10, 9), (8, 8, 8), (12, 15, 7), (20, 16, 5),
+          (64, 32, 16), (50, 100, 4)]
+
+
+@pytest.mark.parametrize("dims", PSIZES)
+def test_preconditioner_fp64_fp32(dims):
+    need_gpu()
+    F = lib()
+    nx, ny, nt = dims
+    p = params(nx, ny, nt, gamma=1e-4)
+    o = O.AdmmOptions(delta=0.4, rho=1.618)
+    fo = F.AdmmOptions(delta=0.4, rho=1.618)
+    prob = F.Problem(p)
+    r = fi.random_field(9, (nt, nx, ny))
+    ref = O.apply_preconditioner(p, o, r)
+    got = host(prob.precond(dev(r), fo))
+    assert relerr(got, ref) < 1e-12
+    got32 = host(prob.precond(dev(r, torch.float32), fo))
+    assert relerr(got32, ref) < 2e-5
+    # in place
+    rd = dev(r)
+    prob.precond(rd, fo, out=rd)
+    assert relerr(host(rd), ref) < 1e-12
+    prob.close()
+
+
+def test_unsupported_preconditioner_length_is_reported():
+    need_gpu()
+    F = lib()
+    prob = F.Problem(params(11, 4, 2))
+    r = dev(np.ones(prob.N))
+    with pytest.raises(F.FdeError) as e:
+        prob.precond(r, F.AdmmOptions())
+    assert e.value.status == F.FDE_EUNSUPPORTED
+    # the matvec supports every length
+    x = fi.random_field(1, prob.shape)
+    assert relerr(host(prob.matvec(dev(x))), O.apply_B(prob.params, x)) < 1e-12
+
+
+def test_invalid_parameters_rejected():
+    need_gpu()
+    F = lib()
+    for bad in (dict(beta_x=2.0), dict(beta_y=1.0), dict(alpha_t=0.0), dict(alpha_t=1.2), dict(gamma=0.0),
+                dict(dp=-1.0)):
+        with pytest.raises(F.FdeError) as e:
+            F.Problem(params(4, 4, 4, **bad))
+        assert e.value.status == F.FDE_EINVAL
+    with pytest.raises(F.FdeError) as e:
+        F.Problem(params(4097, 4, 4))
+    assert e.value.status == F.FDE_EUNSUPPORTED
+    prob = F.Problem(params(4, 4, 4))
+    x = dev(np.zeros(prob.N))
+    with pytest.raises(F.FdeError):
+        prob.matvec(x, op=7)
+    with pytest.raises(F.FdeError):
+        prob.matvec(x, op=F.FDE_OP_S, opts=F.AdmmOptions(rho=1.7))
+    prob.close()
+
+
+@pytest.mark.parametrize("cfg", ["medium", "large"])
+def test_matvec_full_size_sampled(cfg):
+    """B x and B^T x at the 256^2 x 64 and 1024^2 x 128 workloads, FP64 and FP32,
+    checked at sampled points that the oracle evaluates one by one."""
+    need_gpu()
+    F = lib()
+    inst = fi.config_medium() if cfg == "medium" else fi.config_large()
+    p = inst.params
+    prob = F.Problem(p)
+    x = inst.ybar
+    rng = np.random.default_rng(4)
+    pts = [(0, 0, 0), (p.nt - 1, p.nx - 1, p.ny - 1), (p.nt - 1, 0, p.ny - 1)]
+    pts += [tuple(int(rng.integers(0, m)) for m in (p.nt, p.nx, p.ny)) for _ in range(24)]
+    xd = dev(x)
+    for op, tr in ((F.FDE_OP_B, False), (F.FDE_OP_BT, True)):
+        full = host(prob.matvec(xd, op)).reshape(p.nt, p.nx, p.ny)
+        ref = O.apply_B_at(p, x, pts, transpose=tr)
+        got = np.array([full[q] for q in pts])
+        scale = np.max(np.abs(full))
+        assert np.max(np.abs(got - ref)) / scale < 1e-12
+        full32 = host(prob.matvec(xd.float(), op)).reshape(p.nt, p.nx, p.ny)
+        got32 = np.array([full32[q] for q in pts])
+        assert np.max(np.abs(got32 - ref)) / scale < 2e-5
+        del full, full32
+    prob.close()
+    torch.cuda.empty_cache()
