@@ -1,0 +1,323 @@
+"""Benchmark of the ADMM / Toeplitz-FFT hot path on GB300.
+
+One step = one ADMM solve (Algorithm 1, fixed number of iterations, every
+sub-problem S y = rhs solved to 1e-8 relative residual) of the 1024^2 x 128
+workload (beta_x = 1.7, beta_y = 1.2, d = (2.0, 0.1), e = (0.5, 0.5),
+gamma = 1e-6, control box [-1, 1]) in MIXED precision: float FFT operator and
+preconditioner inside double iterative refinement. Inputs are resident in HBM
+and each vector (1.07 GB in double) is far larger than L2, so no flush is
+needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0). --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ADMM solve s & Toeplitz-FFT matvec GB/s at 1024²×128; mixed vs FP64 at 1e-8"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=["large", "medium", "small"])
+    ap.add_argument("--admm-iters", type=int, default=3)
+    ap.add_argument("--sub-tol", type=float, default=1e-8)
+    ap.add_argument("--no-extras", action="store_true", help="skip FP64 comparison, e2e and CPU baseline")
+    return ap.parse_args()
+
+
+def workload(name):
+    import fde_inputs as fi
+    return {"large": fi.config_large, "medium": fi.config_medium, "small": fi.config_small}[name]()
+
+
+def describe(inst, admm_iters, sub_tol):
+    p = inst.params
+    return {
+        "workload": f"{p.nx}x{p.ny}x{p.nt} two-sided space-fractional diffusion, implicit Euler; ADMM "
+                    f"{admm_iters} iterations per solve, sub-solves to {sub_tol:g} relative residual",
+        "nx": p.nx, "ny": p.ny, "nt": p.nt, "N": p.N, "beta": [p.beta_x, p.beta_y], "coef": [p.dp, p.dm, p.ep, p.em],
+        "gamma": p.gamma, "box": {"ya": inst.ya, "yb": inst.yb, "ua": inst.ua, "ub": inst.ub},
+        "delta": 1.0, "rho": 1.618, "precision": "mixed (float FFT operator/preconditioner, double refinement)",
+        "l2": "no flush: every vector (8N bytes = %.2f GB) exceeds the 126 MB L2" % (8 * p.N / 1e9),
+    }
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(inst, pcg_equiv, sample_planes=2):
+    """Time the FP64 oracle's structured operators (one S application and one
+    preconditioner application = one PCG iteration) on `sample_planes` time
+    slices of the workload, scale to the full grid, and multiply by the number
+    of PCG-iteration equivalents of one GPU solve."""
+    import numpy as np
+    import fde_inputs as fi
+    import oracle as O
+    p = inst.params
+    q = fi.FdeParams(**{**p.__dict__, "nt": sample_planes})
+    o = O.AdmmOptions(delta=1.0, rho=1.618)
+    x = inst.ybar[:sample_planes].copy()
+    O.apply_S(q, o, x[:1].copy() if sample_planes == 1 else x)  # warm caches / BLAS threads
+    t0 = time.perf_counter()
+    O.apply_S(q, o, x)
+    O.apply_preconditioner(q, o, x)
+    dt = time.perf_counter() - t0
+    per_iter = dt * p.nt / sample_planes
+    return {
+        "value": per_iter * pcg_equiv, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+        "sample": f"one S product + one preconditioner application of the FP64 oracle on {sample_planes} of "
+                  f"{p.nt} time slices ({dt:.2f} s), scaled x{p.nt / sample_planes:g} to the full grid and "
+                  f"x{pcg_equiv:.1f} PCG-iteration equivalents of one solve",
+        "per_pcg_iter_s": per_iter,
+    }
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    inst = workload(args.workload)
+    # PCG-iteration equivalents of the GPU solve (measured on the GPU arm: about
+    # 15 PCG iterations and 8 double matvecs per ADMM iteration at this workload)
+    pcg_equiv = args.admm_iters * (15 + 4)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(inst, pcg_equiv, sample_planes=1)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.mean(vals)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": describe(inst, args.admm_iters, args.sub_tol), "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1907_13428_gb300 as F
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    inst = workload(args.workload)
+    p = inst.params
+    prob = F.Problem(p)
+    N = prob.N
+    ybar = torch.as_tensor(inst.ybar.ravel(), device=dev)
+    bounds = dict(ya=inst.ya, yb=inst.yb, ua=inst.ua, ub=inst.ub)
+    mixed = F.AdmmOptions(delta=1.0, rho=1.618, max_admm=args.admm_iters, fixed_iters=True, inner_tol_mode=1,
+                          inner_tol=args.sub_tol, precision=F.FDE_MIXED, inner_tol_mixed=1e-4, max_pcg=500,
+                          max_refine=30)
+    out = {k: torch.empty(N, dtype=torch.float64, device=dev) for k in ("y", "u", "p", "zu")}
+
+    def step(opts=mixed):
+        return prob.admm_solve(opts, ybar, out=out, **bounds)
+
+    for _ in range(args.warmup):
+        r = step()
+    stats = r["stats"]
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = F.kernel_launches()
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(args.steps):
+            r = step()
+        e1.record(st)
+        torch.cuda.synchronize()
+        barrier()
+    launches = F.kernel_launches() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ms / 1e3 / world  # seconds per solve, world solves per step (one replica per GPU)
+
+    extras = {}
+    if not args.no_extras:
+        # Toeplitz-FFT matvec (float, y = B x) and the other operator units, timed alone
+        def evtime(fn, reps=5):
+            fn()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            for _ in range(reps):
+                fn()
+            b.record(st)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        x32 = ybar.float()
+        y32 = torch.empty_like(x32)
+        y64 = torch.empty_like(ybar)
+        t_b32 = evtime(lambda: prob.matvec(x32, F.FDE_OP_B, out=y32))
+        t_s32 = evtime(lambda: prob.matvec(x32, F.FDE_OP_S, mixed, out=y32))
+        t_m32 = evtime(lambda: prob.precond(x32, mixed, out=y32))
+        t_b64 = evtime(lambda: prob.matvec(ybar, F.FDE_OP_B, out=y64), reps=3)
+        t_m64 = evtime(lambda: prob.precond(ybar, mixed, out=y64), reps=3)
+        del x32, y32, y64
+        hbm, src = peaks()
+        alg = 8.0 * N  # read x, write y (float)
+        achieved = alg / (t_b32 * 1e-3) / 1e9
+        extras["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                              "frac": achieved / hbm, "traffic": None,
+                              "kernel": "Toeplitz-FFT matvec y = B x, float (x2 pass + x1 pass)",
+                              "peak_source": src, "ms": t_b32}
+        extras["operators_ms"] = {"B_f32": t_b32, "S_f32": t_s32, "precond_f32": t_m32, "B_f64": t_b64,
+                                  "precond_f64": t_m64}
+        # all-FP64 solve with the same iteration count and sub-solve tolerance
+        fp64 = F.AdmmOptions(**{**mixed.__dict__, "precision": F.FDE_FP64})
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        r64 = step(fp64)
+        b.record(st)
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b) / 1e3
+        y64c, u64c = out["y"].clone(), out["u"].clone()
+        r = step()
+        dy = float((out["y"] - y64c).abs().max() / y64c.abs().max())
+        du = float((out["u"] - u64c).abs().max() / u64c.abs().max())
+        del y64c, u64c
+        extras["fp64_compare"] = {"fp64_solve_s": t64, "mixed_solve_s": value * world, "speedup": t64 / (value * world),
+                                  "mixed_vs_fp64_relerr": {"y": dy, "u": du},
+                                  "fp64_stats": r64["stats"], "mixed_stats": r["stats"]}
+        # end to end through host buffers: pinned ybar in, y and u out, every step
+        hy = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        hy.copy_(torch.as_tensor(inst.ybar.ravel()))
+        hout_y = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        hout_u = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(max(1, args.steps // 2)):
+            ybar.copy_(hy, non_blocking=True)
+            rr = step()
+            hout_y.copy_(rr["y"], non_blocking=True)
+            hout_u.copy_(rr["u"], non_blocking=True)
+        b.record(st)
+        torch.cuda.synchronize()
+        te = a.elapsed_time(b) / 1e3 / max(1, args.steps // 2)
+        extras["e2e"] = {"value": te, "unit": "s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 16 * N}
+        if rank == 0:
+            extras["cpu_baseline"] = cpu_baseline(inst, stats["pcg_iters"] + stats["fp64_matvecs"] / 2)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": describe(inst, args.admm_iters, args.sub_tol), "gpu_launches": launches,
+                "clocks": clk.summary(), "solve_stats": stats}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    prob.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

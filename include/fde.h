@@ -183,6 +183,10 @@ const char* fde_strerror(int status);
 /* Text of the last CUDA error seen by this library in the calling thread. */
 const char* fde_last_cuda_error(void);
 
+/* Number of kernel launches this library has issued in this process (all
+ * problems, all threads); a diagnostic counter for profiling and benchmarks. */
+long long fde_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

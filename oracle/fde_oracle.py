@@ -381,6 +381,14 @@ def admm_after_solve(p, o, g, lo_y, hi_y, lo_u, hi_u, st: AdmmState, y, bu, r0):
     return AdmmState(y, u, zy, zu, pn, wy, wu, st.iters + 1, res, st.pcg_iters)
 
 
+def factor_S(p, o: AdmmOptions):
+    """Cholesky factor of S (lower), kept in Fortran order so that every solve
+    reads it in place."""
+    c, lower = sla.cho_factor(np.asfortranarray(assemble_S(p, o)), lower=True, overwrite_a=True,
+                              check_finite=False)
+    return np.asfortranarray(c), lower
+
+
 def admm_direct(inst, o: AdmmOptions, iters: Optional[int] = None, state: Optional[AdmmState] = None,
                 factor=None) -> AdmmState:
     """Algorithm 1 with each sub-problem solved exactly: S is factored once by
@@ -392,11 +400,11 @@ def admm_direct(inst, o: AdmmOptions, iters: Optional[int] = None, state: Option
     lo_y, hi_y = box_bounds(p, inst.ya, inst.yb)
     lo_u, hi_u = box_bounds(p, inst.ua, inst.ub)
     st = zero_state(p) if state is None else state
-    cho = factor if factor is not None else sla.cho_factor(assemble_S(p, o), lower=True)
+    cho = factor if factor is not None else factor_S(p, o)
     n = iters if iters is not None else o.max_iter
     for _ in range(n):
         rhs, bu, r0 = admm_rhs(p, o, inst.ybar, g, st)
-        y = sla.cho_solve(cho, rhs.ravel()).reshape(rhs.shape)
+        y = sla.cho_solve(cho, rhs.ravel(), check_finite=False).reshape(rhs.shape)
         st = admm_after_solve(p, o, g, lo_y, hi_y, lo_u, hi_u, st, y, bu, r0)
         if iters is None and max(st.residuals) <= o.tol:
             break

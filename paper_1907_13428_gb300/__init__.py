@@ -61,6 +61,7 @@ _SIGS = {
     "fde_admm_grad": (ctypes.c_int, [_P, _P, _P, _P, _D, _P, ctypes.POINTER(ctypes.c_double), _P, _P]),
     "fde_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "fde_last_cuda_error": (ctypes.c_char_p, []),
+    "fde_kernel_launches": (ctypes.c_longlong, []),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -80,6 +81,11 @@ def lib() -> ctypes.CDLL:
             f.argtypes = args
         _lib = L
     return _lib
+
+
+def kernel_launches() -> int:
+    """Kernel launches issued by the library so far in this process."""
+    return int(lib().fde_kernel_launches())
 
 
 class FdeError(RuntimeError):

@@ -3,6 +3,7 @@
 // the ADMM driver (Algorithm 1 with the sub-problem merged with the p update,
 // Section 3.1; psi scaling and stopping rules of Section 6.1), and the
 // gradient of the optimal value.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -13,6 +14,11 @@
 using namespace fde;
 
 static thread_local char g_cuda_err[256] = "";
+static std::atomic<long long> g_launches{0};
+
+namespace fde {
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace fde
 
 cudaError_t fde_alloc(fde_problem* P, void** ptr, size_t bytes) {
   if (P->nallocs >= (int)(sizeof(P->allocs) / sizeof(P->allocs[0]))) return cudaErrorMemoryAllocation;
@@ -246,6 +252,8 @@ const char* fde_strerror(int s) {
 }
 
 const char* fde_last_cuda_error(void) { return g_cuda_err; }
+
+long long fde_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 long long fde_size(const fde_problem* P) { return P ? P->N : 0; }
 double fde_psi(const fde_problem* P) { return P ? P->psi : 0.0; }

@@ -64,6 +64,9 @@ struct fde_problem {
 
 namespace fde {
 
+// Process-wide count of kernel launches issued by this library (diagnostics).
+void note_launches(int n);
+
 // Device-scalar slots in fde_problem::dscal.
 enum Scal {
   S_RZ = 0, S_RZ_NEW, S_PQ, S_ALPHA, S_BETA, S_RR, S_BB, S_TMP0, S_TMP1, S_TMP2,

@@ -172,6 +172,7 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
     const long long grid = (np + pairs - 1) / pairs;
     k_prec_rows_fwd<R><<<(unsigned)grid, threads, (size_t)pairs * ny * sizeof(C), st>>>(
         r, spec, nrows, ny, H, Hp, ptables<R>(Ay).twn, Ay.plann, pairs);
+  note_launches(1);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   const int threads = sizeof(R) == 4 ? 1024 : 512;
@@ -213,6 +214,7 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
     k_prec_axis<R><<<(unsigned)grid, threads, (size_t)lines * n * sizeof(C), st>>>(
         spec, n, axis_stride, n_inner, outer_stride, n_outer, ptables<R>(A).twn, A.plann, step == 2 ? 1 : 0, lines,
         dv, ptables<R>(At).lam, ptables<R>(Ax).lam, ptables<R>(Ay).lam);
+  note_launches(1);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   // 5. rows inverse
@@ -225,6 +227,7 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
     const long long grid = (np + pairs - 1) / pairs;
     k_prec_rows_inv<R><<<(unsigned)grid, threads2, (size_t)pairs * ny * sizeof(C), st>>>(
         spec, z, nrows, ny, H, Hp, ptables<R>(Ay).twn, Ay.plann, pairs);
+  note_launches(1);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   return cudaSuccess;

@@ -194,22 +194,36 @@ cudaError_t setup_axis_tables(fde_problem* P, cudaStream_t st) {
     A.f.twn = (float2*)p;
 
     k_twiddle<<<(2 * L + 255) / 256, 256, 0, st>>>(A.d.tw2, 2 * L);
+  note_launches(1);
     k_twiddle<<<(L + 255) / 256, 256, 0, st>>>(A.d.twL, L);
+  note_launches(1);
     k_twiddle<<<(n + 255) / 256, 256, 0, st>>>(A.d.twn, n);
+  note_launches(1);
     k_axis_columns<<<1, 1024, 0, st>>>(s, g, emb, embL, tch);
+  note_launches(1);
     // embedding symbol of order 2L, scaled by coef / (2L), split into halves
     k_dft<<<(2 * L + 127) / 128, 128, 0, st>>>(emb, 2 * L, A.d.tw2, lam2, coef / (2.0 * L));
+  note_launches(1);
     k_halves<<<(2 * L + 255) / 256, 256, 0, st>>>(lam2, L, A.d.sym);
+  note_launches(1);
     // one-sided L alone (unscaled apart from 1/(2L))
     k_dft<<<(2 * L + 127) / 128, 128, 0, st>>>(embL, 2 * L, A.d.tw2, lamL, 1.0 / (2.0 * L));
+  note_launches(1);
     k_halves<<<(2 * L + 255) / 256, 256, 0, st>>>(lamL, L, A.d.symL);
+  note_launches(1);
     // T. Chan eigenvalues of order n
     k_dft<<<(n + 127) / 128, 128, 0, st>>>(tch, n, A.d.twn, A.d.lam, 1.0);
+  note_launches(1);
     k_to_float2<<<(2 * L + 255) / 256, 256, 0, st>>>(A.d.sym, A.f.sym, 2 * L);
+  note_launches(1);
     k_to_float2<<<(2 * L + 255) / 256, 256, 0, st>>>(A.d.tw2, A.f.tw2, 2 * L);
+  note_launches(1);
     k_to_float2<<<(L + 255) / 256, 256, 0, st>>>(A.d.twL, A.f.twL, L);
+  note_launches(1);
     k_to_float2<<<(n + 255) / 256, 256, 0, st>>>(A.d.lam, A.f.lam, n);
+  note_launches(1);
     k_to_float2<<<(n + 255) / 256, 256, 0, st>>>(A.d.twn, A.f.twn, n);
+  note_launches(1);
     if ((e = cudaGetLastError())) return e;
     // scratch is reused by the next axis: wait for this one
     if ((e = cudaStreamSynchronize(st))) return e;

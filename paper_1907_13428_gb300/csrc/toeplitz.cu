@@ -185,6 +185,7 @@ static cudaError_t launch_rows(fde_problem* P, const R* x, R* out, int conj_sym,
   const size_t smem = (size_t)2 * pairs * L * sizeof(cplx<R>);
   k_rows<R><<<(unsigned)grid, threads, smem, st>>>(x, out, nrows, A.n, L, sym ? sym : T.sym, T.tw2, T.twL,
                                                    A.planL, conj_sym, pairs);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -216,6 +217,7 @@ static cudaError_t launch_axis(fde_problem* P, int axis, const R* x, int conj_sy
   const size_t smem = (size_t)2 * pairs * L * sizeof(cplx<R>);
   k_axis<R><<<(unsigned)grid, threads, smem, st>>>(x, A.n, L, axis_stride, n_inner, outer_stride, n_outer,
                                                    sym ? sym : T.sym, T.tw2, T.twL, A.planL, conj_sym, pairs, E);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -284,7 +284,9 @@ template <typename RA, typename RB>
 cudaError_t dot(fde_problem* P, const RA* a, const RB* b, long long n, int slot, int op, cudaStream_t st) {
   const int g = red_grid(n);
   k_dot<RA, RB><<<g, kRedThreads, 0, st>>>(a, b, n, P->partials);
+  note_launches(1);
   k_finish<<<1, 1024, 0, st>>>(P->partials, g, P->dscal, slot, op);
+  note_launches(1);
   return cudaGetLastError();
 }
 template cudaError_t dot<double, double>(fde_problem*, const double*, const double*, long long, int, int, cudaStream_t);
@@ -294,7 +296,9 @@ template <typename RV>
 cudaError_t pcg_xr(fde_problem* P, RV* x, RV* r, const RV* d, const RV* q, long long n, cudaStream_t st) {
   const int g = red_grid(n);
   k_pcg_xr<RV><<<g, kRedThreads, 0, st>>>(x, r, d, q, P->dscal, n, P->partials);
+  note_launches(1);
   k_finish<<<1, 1024, 0, st>>>(P->partials, g, P->dscal, S_RR, FIN_STORE);
+  note_launches(1);
   return cudaGetLastError();
 }
 template cudaError_t pcg_xr<double>(fde_problem*, double*, double*, const double*, const double*, long long,
@@ -304,6 +308,7 @@ template cudaError_t pcg_xr<float>(fde_problem*, float*, float*, const float*, c
 template <typename RV>
 cudaError_t pcg_p(fde_problem* P, RV* d, const RV* z, long long n, cudaStream_t st) {
   k_pcg_p<RV><<<sgrid(n), 256, 0, st>>>(d, z, P->dscal, n);
+  note_launches(1);
   return cudaGetLastError();
 }
 template cudaError_t pcg_p<double>(fde_problem*, double*, const double*, long long, cudaStream_t);
@@ -313,21 +318,26 @@ cudaError_t residual(fde_problem* P, const double* b, const double* s, double* r
                      cudaStream_t st) {
   const int g = red_grid(n);
   k_residual<<<g, kRedThreads, 0, st>>>(b, s, r, n, P->partials);
+  note_launches(1);
   k_finish<<<1, 1024, 0, st>>>(P->partials, g, P->dscal, slot, FIN_STORE);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t to_f32(const double* in, float* out, long long n, cudaStream_t st) {
   k_to_f32<<<sgrid(n), 256, 0, st>>>(in, out, n);
+  note_launches(1);
   return cudaGetLastError();
 }
 cudaError_t add_f32(double* y, const float* d, long long n, cudaStream_t st) {
   k_add_f32<<<sgrid(n), 256, 0, st>>>(y, d, n);
+  note_launches(1);
   return cudaGetLastError();
 }
 template <typename R>
 cudaError_t fill(R* x, R v, long long n, cudaStream_t st) {
   k_fill<R><<<sgrid(n), 256, 0, st>>>(x, v, n);
+  note_launches(1);
   return cudaGetLastError();
 }
 template cudaError_t fill<double>(double*, double, long long, cudaStream_t);
@@ -335,6 +345,7 @@ template cudaError_t fill<float>(float*, float, long long, cudaStream_t);
 template <typename R>
 cudaError_t copy(R* dst, const R* src, long long n, cudaStream_t st) {
   k_copy<R><<<sgrid(n), 256, 0, st>>>(dst, src, n);
+  note_launches(1);
   return cudaGetLastError();
 }
 template cudaError_t copy<double>(double*, const double*, long long, cudaStream_t);
@@ -342,6 +353,7 @@ template cudaError_t copy<float>(float*, const float*, long long, cudaStream_t);
 
 cudaError_t admm_pre(const AdmmArgs& A, double* c, double* bu, double* r0, double* q, cudaStream_t st) {
   k_admm_pre<<<sgrid(A.n), 256, 0, st>>>(A, c, bu, r0, q);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -350,13 +362,16 @@ cudaError_t admm_post(fde_problem* P, const AdmmArgs& A, const double* y, const 
   int g = red_grid(A.n);
   if (g > kMaxPartials / 5) g = kMaxPartials / 5;
   k_admm_post<<<g, kRedThreads, 0, st>>>(A, y, By, bu, r0, u, P->partials, g);
+  note_launches(1);
   k_admm_finish<<<1, 1024, 0, st>>>(P->partials, g, P->dscal);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t grad_ybar(const double* y, const double* ybar, const double* wy, double w0, double w1, long long last_start,
                       long long n, double* dJ, double* f, cudaStream_t st) {
   k_grad_ybar<<<sgrid(n), 256, 0, st>>>(y, ybar, wy, w0, w1, last_start, n, dJ, f);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -113,7 +113,9 @@ def test_admm_small_workload_converges():
     need_gpu()
     F = lib()
     inst = fi.config_small()
-    fo = F.AdmmOptions(delta=1.0, rho=1.618, tol_admm=1e-6, max_admm=2000, inner_tol_mode=0, precision=F.FDE_MIXED)
+    # ADMM needs about 2e4 iterations here (delta = 1): the residuals of the
+    # oracle's exact-sub-solve iteration fall by ~8% per 100 iterations
+    fo = F.AdmmOptions(delta=1.0, rho=1.618, tol_admm=1e-6, max_admm=40000, inner_tol_mode=0, precision=F.FDE_MIXED)
     r = _run(F, inst, fo)
     s = r["stats"]
     assert r["status"] == F.FDE_OK, s
