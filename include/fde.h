@@ -177,6 +177,28 @@ int fde_admm_solve(fde_problem* prob, const fde_admm_opts* opts,
 int fde_admm_grad(fde_problem* prob, const double* y, const double* ybar, const double* wy,
                   double tol, double* dJ_dybar, double* dJ_dcoef, double* p_out, void* stream);
 
+/* Largest problem (nt*nx*ny points) fde_matvec_noalloc accepts. */
+#define FDE_NOALLOC_MAX_N 1048576LL
+
+/* y = B x (op FDE_OP_B) or y = B^T x (FDE_OP_BT) in double precision, without
+ * any device allocation. The paper has no counterpart to this entry point: it
+ * exists for callers that cannot call cudaMalloc, such as a plug-in running
+ * inside a framework whose caching allocator owns the device memory, or a
+ * latency-critical serving path that must not allocate (cudaMalloc can
+ * synchronise the device and can fail under memory pressure). It computes the
+ * same product as fde_matvec, with no fde_problem: the caller passes `params`
+ * and its own x and y (device, double, length N). All other buffers (the
+ * intermediates of the transform passes and the symbol/twiddle tables, rebuilt
+ * from `params` on every call) live in one fixed device array of about 18 MB
+ * that every GPU loading this library holds until the process exits.
+ * Errors: FDE_EINVAL (as fde_setup, or op not B/B^T, or x == y),
+ * FDE_EUNSUPPORTED (N > FDE_NOALLOC_MAX_N or an axis above 4096), FDE_ECUDA.
+ * The first call on each device looks up the array's device address and sets
+ * kernel attributes; make it before any stream capture. All calls share the
+ * array: calls whose GPU work overlaps (two streams or host threads) race and
+ * must be serialised by the caller. The work is queued on `stream`. */
+int fde_matvec_noalloc(const fde_params* params, int op, const double* x, double* y, void* stream);
+
 /* Static message for a status code. */
 const char* fde_strerror(int status);
 

@@ -62,6 +62,7 @@ _SIGS = {
     "fde_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "fde_last_cuda_error": (ctypes.c_char_p, []),
     "fde_kernel_launches": (ctypes.c_longlong, []),
+    "fde_matvec_noalloc": (ctypes.c_int, [ctypes.POINTER(fde_params), ctypes.c_int, _P, _P, _P]),
 }
 EXPORTED = tuple(_SIGS)
 
