@@ -1,0 +1,233 @@
+// Register-resident Stockham FFT for power-of-two lengths 16 <= L <= 4096.
+//
+// A line of length L is held by T = L/16 threads, 16 complex values each.
+// The forward transform runs radix-16 passes and a last pass of radix
+// RL = L / 16^(P-1) in {2, 4, 8, 16}; the inverse runs the radices in the
+// opposite order. With the Stockham indexing (butterfly j reads j + r L/R,
+// multiplies by W_{Ns R}^{r (j mod Ns)}, writes (j div Ns) Ns R + (j mod Ns) + r Ns)
+// the registers of thread t hold
+//   before the forward transform and after the inverse: positions t + r T;
+//   after the forward transform and before the inverse:  positions
+//     t + T q + r L/RL  (butterfly q < 16/RL, element r < RL),
+// so the last forward pass and the first inverse pass touch the same values
+// and a pointwise multiply in frequency needs no data exchange. Between the
+// other passes the values go through shared memory (write, barrier, read,
+// barrier). P = 1, 2, 3 passes for L = 16, 32..256, 512..4096.
+#pragma once
+#include "common.cuh"
+
+namespace fde {
+
+template <int L> struct RfShape {
+  static constexpr int T = L / 16;
+  static constexpr int P = (L <= 16) ? 1 : (L <= 256 ? 2 : 3);
+  static constexpr int RL = (P == 1) ? 16 : (P == 2 ? L / 16 : L / 256);
+  static_assert(L >= 16 && L <= 4096 && (L & (L - 1)) == 0, "power of two in [16, 4096]");
+};
+
+// a * W_16^M (forward) or a * conj(W_16^M) (inverse), W_16 = exp(-2 pi i / 16)
+template <typename C, int M, bool INV>
+__device__ __forceinline__ C w16(C a) {
+  using R = decltype(C::x);
+  constexpr int m = M & 15;
+  constexpr R h = (R)0.70710678118654752440;
+  constexpr R c1 = (R)0.92387953251128675613;  // cos(pi/8)
+  constexpr R s1 = (R)0.38268343236508977173;  // sin(pi/8)
+  if constexpr (m == 0) {
+    return a;
+  } else if constexpr (m == 8) {
+    return mk<C>(-a.x, -a.y);
+  } else if constexpr (m == 4) {
+    return INV ? mk<C>(-a.y, a.x) : mk<C>(a.y, -a.x);
+  } else if constexpr (m == 12) {
+    return INV ? mk<C>(a.y, -a.x) : mk<C>(-a.y, a.x);
+  } else {
+    // cos(pi m / 8), sin(pi m / 8) for the remaining m
+    constexpr R cs[16] = {1, c1, h, s1, 0, -s1, -h, -c1, -1, -c1, -h, -s1, 0, s1, h, c1};
+    constexpr R sn[16] = {0, s1, h, c1, 1, c1, h, s1, 0, -s1, -h, -c1, -1, -c1, -h, -s1};
+    constexpr R c = cs[m];
+    constexpr R s = INV ? -sn[m] : sn[m];
+    // (a.x + i a.y)(c - i s)
+    return mk<C>(a.x * c + a.y * s, a.y * c - a.x * s);
+  }
+}
+
+template <typename C, bool INV>
+__device__ __forceinline__ void dft2(C& a0, C& a1) {
+  const C t = a0;
+  a0 = cadd(t, a1);
+  a1 = csub(t, a1);
+}
+
+template <typename C, bool INV>
+__device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+  const C s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  const C s13 = cadd(a1, a3), d13 = csub(a1, a3);
+  const C rot = INV ? mul_pi(d13) : mul_mi(d13);
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, rot);
+  a3 = csub(d02, rot);
+}
+
+// in-place 8-point DFT of v[0..7] (natural order in and out)
+template <typename C, bool INV>
+__device__ __forceinline__ void dft8(C* v) {
+  C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<C, INV>(e0, e1, e2, e3);
+  dft4<C, INV>(o0, o1, o2, o3);
+  o1 = w16<C, 2, INV>(o1);
+  o2 = w16<C, 4, INV>(o2);
+  o3 = w16<C, 6, INV>(o3);
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1);
+  v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2);
+  v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3);
+  v[7] = csub(e3, o3);
+}
+
+// in-place 16-point DFT of v[0..15]: 4-point DFTs over n1 (n = n2 + 4 n1),
+// twiddles W16^{n2 k1}, 4-point DFTs over n2; output index k1 + 4 k2.
+template <typename C, bool INV>
+__device__ __forceinline__ void dft16(C* v) {
+  dft4<C, INV>(v[0], v[4], v[8], v[12]);
+  dft4<C, INV>(v[1], v[5], v[9], v[13]);
+  dft4<C, INV>(v[2], v[6], v[10], v[14]);
+  dft4<C, INV>(v[3], v[7], v[11], v[15]);
+  // b[n2][k1] sits at v[n2 + 4 k1]
+  v[5] = w16<C, 1, INV>(v[5]);
+  v[9] = w16<C, 2, INV>(v[9]);
+  v[13] = w16<C, 3, INV>(v[13]);
+  v[6] = w16<C, 2, INV>(v[6]);
+  v[10] = w16<C, 4, INV>(v[10]);
+  v[14] = w16<C, 6, INV>(v[14]);
+  v[7] = w16<C, 3, INV>(v[7]);
+  v[11] = w16<C, 6, INV>(v[11]);
+  v[15] = w16<C, 9, INV>(v[15]);
+  // outer DFTs over n2 for each k1: inputs v[4 k1 + n2]
+  dft4<C, INV>(v[0], v[1], v[2], v[3]);
+  dft4<C, INV>(v[4], v[5], v[6], v[7]);
+  dft4<C, INV>(v[8], v[9], v[10], v[11]);
+  dft4<C, INV>(v[12], v[13], v[14], v[15]);
+  // now X[k1 + 4 k2] sits at v[4 k1 + k2]: transpose the 4x4 index
+  C t;
+  t = v[1]; v[1] = v[4]; v[4] = t;
+  t = v[2]; v[2] = v[8]; v[8] = t;
+  t = v[3]; v[3] = v[12]; v[12] = t;
+  t = v[6]; v[6] = v[9]; v[9] = t;
+  t = v[7]; v[7] = v[13]; v[13] = t;
+  t = v[11]; v[11] = v[14]; v[14] = t;
+}
+
+template <typename C, int RAD, bool INV>
+__device__ __forceinline__ void dftR(C* v) {
+  if constexpr (RAD == 2) dft2<C, INV>(v[0], v[1]);
+  else if constexpr (RAD == 4) dft4<C, INV>(v[0], v[1], v[2], v[3]);
+  else if constexpr (RAD == 8) dft8<C, INV>(v);
+  else dft16<C, INV>(v);
+}
+
+// One pass' arithmetic on the 16 values of thread t: butterflies q < 16/RAD,
+// j = t + T q, twiddles W_{Ns RAD}^{r (j mod Ns)} from tw = W_L^m, then DFT.
+template <typename R, int L, int RAD, bool INV, int NL>
+__device__ __forceinline__ void rf_compute(cplx<R> (&v)[NL][16], int t, int Ns, const cplx<R>* __restrict__ tw) {
+  using C = cplx<R>;
+  constexpr int T = L / 16;
+  constexpr int B = 16 / RAD;
+#pragma unroll
+  for (int q = 0; q < B; ++q) {
+    if (Ns > 1) {
+      const int j = t + T * q;
+      const int k = j & (Ns - 1);
+      const int step = L / (Ns * RAD);
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) {
+        C w = __ldg(&tw[r * k * step]);
+        if (INV) w.y = -w.y;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) v[l][q * RAD + r] = cmul(v[l][q * RAD + r], w);
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < NL; ++l) dftR<C, RAD, INV>(&v[l][q * RAD]);
+  }
+}
+
+// Shared-memory exchange: write the outputs of a pass (radix RAD, Ns), barrier,
+// read the inputs of the next pass (radix RADN), barrier. `at(l, pos)` maps a
+// line and a position to a shared-memory element.
+template <typename R, int L, int RAD, int RADN, int NL, class At>
+__device__ __forceinline__ void rf_exchange(cplx<R> (&v)[NL][16], int t, int Ns, At at) {
+  constexpr int T = L / 16;
+#pragma unroll
+  for (int q = 0; q < 16 / RAD; ++q) {
+    const int j = t + T * q;
+    const int base = (j / Ns) * Ns * RAD + (j & (Ns - 1));
+#pragma unroll
+    for (int r = 0; r < RAD; ++r)
+#pragma unroll
+      for (int l = 0; l < NL; ++l) at(l, base + r * Ns) = v[l][q * RAD + r];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16 / RADN; ++q) {
+    const int j = t + T * q;
+#pragma unroll
+    for (int r = 0; r < RADN; ++r)
+#pragma unroll
+      for (int l = 0; l < NL; ++l) v[l][q * RADN + r] = at(l, j + r * (L / RADN));
+  }
+  __syncthreads();
+}
+
+// Forward transform: positions t + r T  ->  t + T q + r L/RL.
+template <typename R, int L, int NL, class At>
+__device__ __forceinline__ void rf_forward(cplx<R> (&v)[NL][16], int t, const cplx<R>* __restrict__ tw, At at) {
+  using S = RfShape<L>;
+  if constexpr (S::P == 1) {
+    rf_compute<R, L, 16, false, NL>(v, t, 1, tw);
+  } else if constexpr (S::P == 2) {
+    rf_compute<R, L, 16, false, NL>(v, t, 1, tw);
+    rf_exchange<R, L, 16, S::RL, NL>(v, t, 1, at);
+    rf_compute<R, L, S::RL, false, NL>(v, t, 16, tw);
+  } else {
+    rf_compute<R, L, 16, false, NL>(v, t, 1, tw);
+    rf_exchange<R, L, 16, 16, NL>(v, t, 1, at);
+    rf_compute<R, L, 16, false, NL>(v, t, 16, tw);
+    rf_exchange<R, L, 16, S::RL, NL>(v, t, 16, at);
+    rf_compute<R, L, S::RL, false, NL>(v, t, 256, tw);
+  }
+}
+
+// Inverse (unnormalised) transform: positions t + T q + r L/RL  ->  t + r T.
+template <typename R, int L, int NL, class At>
+__device__ __forceinline__ void rf_inverse(cplx<R> (&v)[NL][16], int t, const cplx<R>* __restrict__ tw, At at) {
+  using S = RfShape<L>;
+  if constexpr (S::P == 1) {
+    rf_compute<R, L, 16, true, NL>(v, t, 1, tw);
+  } else if constexpr (S::P == 2) {
+    rf_compute<R, L, S::RL, true, NL>(v, t, 1, tw);
+    rf_exchange<R, L, S::RL, 16, NL>(v, t, 1, at);
+    rf_compute<R, L, 16, true, NL>(v, t, S::RL, tw);
+  } else {
+    rf_compute<R, L, S::RL, true, NL>(v, t, 1, tw);
+    rf_exchange<R, L, S::RL, 16, NL>(v, t, 1, at);
+    rf_compute<R, L, 16, true, NL>(v, t, S::RL, tw);
+    rf_exchange<R, L, 16, 16, NL>(v, t, S::RL, at);
+    rf_compute<R, L, 16, true, NL>(v, t, 16 * S::RL, tw);
+  }
+}
+
+// Frequency position held in v[.][q RL + r] after rf_forward.
+template <int L>
+__device__ __forceinline__ int rf_freq(int t, int idx) {
+  using S = RfShape<L>;
+  const int q = idx / S::RL, r = idx - q * S::RL;
+  return t + S::T * q + r * (L / S::RL);
+}
+
+}  // namespace fde

@@ -153,6 +153,13 @@ __global__ void __launch_bounds__(1024) k_prec_axis(cplx<R>* __restrict__ spec, 
 }
 
 template <typename R>
+cudaError_t launch_prec_axis_reg(int L, cplx<R>* spec, long long axis_stride, long long n_inner,
+                                 long long outer_stride, long long n_outer, const cplx<R>* twn, int mode,
+                                 const DivArgs& dv, const cplx<R>* lt, const cplx<R>* lx, const cplx<R>* ly,
+                                 cudaStream_t st);
+cudaError_t precond_reg_set_smem_attrs();
+
+template <typename R>
 cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const R* r, R* z, cplx<R>* spec,
                           cudaStream_t st) {
   using C = cplx<R>;
@@ -211,6 +218,14 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
       dv.Hp = Hp;
       dv.H = H;
     }
+    const bool pow2 = n >= 16 && (n & (n - 1)) == 0;
+    if (pow2) {
+      err = launch_prec_axis_reg<R>(n, spec, axis_stride, n_inner, outer_stride, n_outer, ptables<R>(A).twn,
+                                    tpass ? 2 : (step == 2 ? 1 : 0), dv, ptables<R>(At).lam, ptables<R>(Ax).lam,
+                                    ptables<R>(Ay).lam, st);
+      if (err != cudaSuccess) return err;
+      continue;
+    }
     k_prec_axis<R><<<(unsigned)grid, threads, (size_t)lines * n * sizeof(C), st>>>(
         spec, n, axis_stride, n_inner, outer_stride, n_outer, ptables<R>(A).twn, A.plann, step == 2 ? 1 : 0, lines,
         dv, ptables<R>(At).lam, ptables<R>(Ax).lam, ptables<R>(Ay).lam);
@@ -252,7 +267,147 @@ cudaError_t precond_set_smem_attrs() {
   if (e) return e;
   e = cudaFuncSetAttribute(k_prec_axis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e) return e;
-  return cudaFuncSetAttribute(k_prec_axis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  e = cudaFuncSetAttribute(k_prec_axis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if (e) return e;
+  return precond_reg_set_smem_attrs();
+}
+
+}  // namespace fde
+
+// ===========================================================================
+// Register-resident column transforms for power-of-two lengths >= 16
+// (fftreg.cuh). Lanes run over columns (coalesced); shared memory is
+// position-major, CP columns per position row, with the physical row
+// pos ^ parity(pos bits 1..4) so that the two position groups of every
+// half-warp (quarter-warp for double) land in different bank halves.
+// mode 0: forward (natural order in, frequency layout out),
+// mode 1: inverse, mode 2: forward, divide by N sigma, inverse.
+// ===========================================================================
+#include "fftreg.cuh"
+
+namespace fde {
+
+template <typename R, int L, int NT>
+__global__ void __launch_bounds__(NT) k_prec_axis_reg(cplx<R>* __restrict__ spec, long long axis_stride,
+                                                       long long n_inner, long long outer_stride, long long n_outer,
+                                                       const cplx<R>* __restrict__ twn, int mode, DivArgs dv,
+                                                       const cplx<R>* __restrict__ lt, const cplx<R>* __restrict__ lx,
+                                                       const cplx<R>* __restrict__ ly) {
+  using C = cplx<R>;
+  constexpr int T = L / 16, CP = NT / T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int cl = threadIdx.x % CP, t = threadIdx.x / CP;
+  const long long total = n_outer * n_inner;
+  const long long q = (long long)blockIdx.x * CP + cl;
+  const bool valid = q < total;
+  const long long o = valid ? q / n_inner : 0;
+  const long long c = valid ? q - o * n_inner : 0;
+  const long long base = o * outer_stride + c;
+  auto at = [sm, cl](int, int pos) -> C& {
+    const int phys = pos ^ (__popc(pos & 30) & 1);
+    return sm[phys * CP + cl];
+  };
+  C v[1][16];
+  if (mode == 1) {
+#pragma unroll
+    for (int idx = 0; idx < 16; ++idx) {
+      const int p = rf_freq<L>(t, idx);
+      v[0][idx] = valid ? spec[base + p * axis_stride] : mk<C>(0, 0);
+    }
+    rf_inverse<R, L, 1>(v, t, twn, at);
+  } else {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int p = t + r * T;
+      v[0][r] = valid ? spec[base + p * axis_stride] : mk<C>(0, 0);
+    }
+    rf_forward<R, L, 1>(v, t, twn, at);
+    if (mode == 2) {
+      const int i = (int)(c / dv.Hp), j = (int)(c - (long long)i * dv.Hp);
+      const bool pad = j >= dv.H;
+      const C b = pad ? mk<C>(0, 0) : __ldg(&lx[i]);
+      const C d = pad ? mk<C>(0, 0) : __ldg(&ly[j]);
+#pragma unroll
+      for (int idx = 0; idx < 16; ++idx) {
+        const int k = rf_freq<L>(t, idx);
+        const C a = __ldg(&lt[k]);
+        const double lr = dv.psi * ((double)a.x - (double)b.x - (double)d.x);
+        const double li = dv.psi * ((double)a.y - (double)b.y - (double)d.y);
+        const double mag = lr * lr + li * li;
+        const double sigma = dv.adjoint ? mag : dv.m1 + mag * dv.inv_m2;
+        const R sc = pad ? (R)0 : (R)(dv.inv_N / sigma);
+        v[0][idx] = cscale(v[0][idx], sc);
+      }
+      rf_inverse<R, L, 1>(v, t, twn, at);
+    }
+  }
+  if (!valid) return;
+  if (mode == 0) {
+#pragma unroll
+    for (int idx = 0; idx < 16; ++idx) spec[base + rf_freq<L>(t, idx) * axis_stride] = v[0][idx];
+  } else {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) spec[base + (t + r * T) * axis_stride] = v[0][r];
+  }
+}
+
+template <typename R> constexpr int prec_nt() { return sizeof(R) == 4 ? 512 : 256; }
+
+template <typename R, int L>
+static cudaError_t launch_prec_axis_reg_L(cplx<R>* spec, long long axis_stride, long long n_inner,
+                                          long long outer_stride, long long n_outer, const cplx<R>* twn, int mode,
+                                          const DivArgs& dv, const cplx<R>* lt, const cplx<R>* lx, const cplx<R>* ly,
+                                          cudaStream_t st) {
+  constexpr int NT = prec_nt<R>();
+  constexpr int CP = NT / (L / 16);
+  const long long total = n_outer * n_inner;
+  const long long grid = (total + CP - 1) / CP;
+  const size_t smem = (size_t)L * CP * sizeof(cplx<R>);
+  k_prec_axis_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(spec, axis_stride, n_inner, outer_stride, n_outer,
+                                                              twn, mode, dv, lt, lx, ly);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+#define FDE_FOR_EACH_PL(M) M(16) M(32) M(64) M(128) M(256) M(512) M(1024) M(2048) M(4096)
+
+template <typename R>
+cudaError_t launch_prec_axis_reg(int L, cplx<R>* spec, long long axis_stride, long long n_inner,
+                                 long long outer_stride, long long n_outer, const cplx<R>* twn, int mode,
+                                 const DivArgs& dv, const cplx<R>* lt, const cplx<R>* lx, const cplx<R>* ly,
+                                 cudaStream_t st) {
+  switch (L) {
+#define FDE_CASE(LL)                                                                                            \
+  case LL:                                                                                                      \
+    return launch_prec_axis_reg_L<R, LL>(spec, axis_stride, n_inner, outer_stride, n_outer, twn, mode, dv, lt, lx, \
+                                         ly, st);
+    FDE_FOR_EACH_PL(FDE_CASE)
+#undef FDE_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_prec_axis_reg<float>(int, float2*, long long, long long, long long, long long,
+                                                 const float2*, int, const DivArgs&, const float2*, const float2*,
+                                                 const float2*, cudaStream_t);
+template cudaError_t launch_prec_axis_reg<double>(int, double2*, long long, long long, long long, long long,
+                                                  const double2*, int, const DivArgs&, const double2*,
+                                                  const double2*, const double2*, cudaStream_t);
+
+cudaError_t precond_reg_set_smem_attrs() {
+  const int big = 200 * 1024;
+  cudaError_t e = cudaSuccess;
+#define FDE_ATTR(LL)                                                                              \
+  if (e == cudaSuccess)                                                                           \
+    e = cudaFuncSetAttribute(k_prec_axis_reg<float, LL, prec_nt<float>()>,                        \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);                   \
+  if (e == cudaSuccess)                                                                           \
+    e = cudaFuncSetAttribute(k_prec_axis_reg<double, LL, prec_nt<double>()>,                      \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  FDE_FOR_EACH_PL(FDE_ATTR)
+#undef FDE_ATTR
+  return e;
 }
 
 }  // namespace fde

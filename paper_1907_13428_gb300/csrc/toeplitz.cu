@@ -162,6 +162,16 @@ __global__ void __launch_bounds__(1024) k_axis(const R* __restrict__ x, int n, i
   }
 }
 
+// Register-resident variants (defined below) used for power-of-two L >= 16.
+template <typename R>
+cudaError_t launch_rows_reg(fde_problem* P, const R* x, R* out, int conj_sym, const cplx<R>* sym,
+                            const AxisTables<R>& T, cudaStream_t st);
+template <typename R>
+cudaError_t launch_axis_reg(int L, const R* x, int n, long long axis_stride, long long n_inner,
+                            long long outer_stride, long long n_outer, const cplx<R>* sym, const AxisTables<R>& T,
+                            int conj_sym, const AxisEpi<R>& E, cudaStream_t st);
+cudaError_t toeplitz_reg_set_smem_attrs();
+
 template <typename R> static const AxisTables<R>& tables(const Axis& A);
 template <> const AxisTables<double>& tables<double>(const Axis& A) { return A.d; }
 template <> const AxisTables<float>& tables<float>(const Axis& A) { return A.f; }
@@ -174,6 +184,7 @@ static cudaError_t launch_rows(fde_problem* P, const R* x, R* out, int conj_sym,
   const Axis& A = P->ax[2];
   const AxisTables<R>& T = tables<R>(A);
   const int L = A.L;
+  if (L >= 16) return launch_rows_reg<R>(P, x, out, conj_sym, sym ? sym : T.sym, T, st);
   const int threads = rows_threads<R>(L);
   const int cap = kEPT * threads;  // complex elements per CTA
   int pairs = cap / (2 * L);
@@ -211,6 +222,9 @@ static cudaError_t launch_axis(fde_problem* P, int axis, const R* x, int conj_sy
     outer_stride = 0;
     n_outer = 1;
   }
+  if (L >= 16)
+    return launch_axis_reg<R>(L, x, A.n, axis_stride, n_inner, outer_stride, n_outer, sym ? sym : T.sym, T, conj_sym,
+                              E, st);
   const long long total = n_outer * ((n_inner + 1) / 2);
   if (pairs > total) pairs = (int)total;
   const long long grid = (total + pairs - 1) / pairs;
@@ -301,6 +315,225 @@ cudaError_t toeplitz_set_smem_attrs() {
   if ((e = cudaFuncSetAttribute(k_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_axis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-  return cudaFuncSetAttribute(k_axis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  if ((e = cudaFuncSetAttribute(k_axis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  return toeplitz_reg_set_smem_attrs();
 }
+}  // namespace fde
+
+// ===========================================================================
+// Register-resident variants (power-of-two L >= 16): each thread holds 16
+// values of both embedding halves of one complex line (fftreg.cuh).
+// ===========================================================================
+#include "fftreg.cuh"
+
+namespace fde {
+
+// x2 axis. NT threads = PAIRS row pairs x T threads per line; thread t of a
+// pair holds positions t + r T of the pair's two half-lines. Shared memory is
+// line-major with one pad element per 16 (conflict-free exchanges).
+template <typename R, int L, int NT>
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const R* __restrict__ x, R* __restrict__ out, long long nrows,
+                                                  int n, const cplx<R>* __restrict__ sym,
+                                                  const cplx<R>* __restrict__ tw2, const cplx<R>* __restrict__ twL,
+                                                  int conj_sym) {
+  using C = cplx<R>;
+  constexpr int T = L / 16, PAIRS = NT / T, LS = L + L / 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int pr = threadIdx.x / T, t = threadIdx.x - pr * T;
+  const long long ra = ((long long)blockIdx.x * PAIRS + pr) * 2, rb = ra + 1;
+  C* my = sm + pr * 2 * LS;
+  auto at = [my](int l, int pos) -> C& { return my[l * LS + pos + (pos >> 4)]; };
+  C v[2][16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int p = t + r * T;
+    R a = 0, b = 0;
+    if (p < n) {
+      if (ra < nrows) a = x[ra * n + p];
+      if (rb < nrows) b = x[rb * n + p];
+    }
+    v[0][r] = mk<C>(a, b);
+    v[1][r] = p < n ? cmul(v[0][r], __ldg(&tw2[p])) : mk<C>(0, 0);
+  }
+  rf_forward<R, L, 2>(v, t, twL, at);
+#pragma unroll
+  for (int idx = 0; idx < 16; ++idx) {
+    const int k = rf_freq<L>(t, idx);
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      C w = __ldg(&sym[l * L + k]);
+      if (conj_sym) w.y = -w.y;
+      v[l][idx] = cmul(v[l][idx], w);
+    }
+  }
+  rf_inverse<R, L, 2>(v, t, twL, at);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int p = t + r * T;
+    if (p < n) {
+      const C res = cadd(v[0][r], cmul(v[1][r], cconj(__ldg(&tw2[p]))));
+      if (ra < nrows) out[ra * n + p] = res.x;
+      if (rb < nrows) out[rb * n + p] = res.y;
+    }
+  }
+}
+
+// Strided axis. NT threads = CP column pairs x T; lanes run over column pairs
+// (coalesced global access). Shared memory is position-major with the two
+// halves' lines side by side; the line index is XOR-swizzled by the parity of
+// the low five position bits, which separates the two position groups of every
+// half-warp into different banks.
+template <typename R, int L, int NT>
+__global__ void __launch_bounds__(NT) k_axis_reg(const R* __restrict__ x, int n, long long axis_stride,
+                                                  long long n_inner, long long outer_stride, long long n_outer,
+                                                  const cplx<R>* __restrict__ sym, const cplx<R>* __restrict__ tw2,
+                                                  const cplx<R>* __restrict__ twL, int conj_sym, AxisEpi<R> E) {
+  using C = cplx<R>;
+  constexpr int T = L / 16, CP = NT / T, LW = 2 * CP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int cl = threadIdx.x % CP, t = threadIdx.x / CP;
+  const long long npi = (n_inner + 1) / 2;
+  const long long total = n_outer * npi;
+  const long long q = (long long)blockIdx.x * CP + cl;
+  const bool valid = q < total;
+  const long long o = valid ? q / npi : 0;
+  const long long c = valid ? 2 * (q - o * npi) : 0;
+  const long long base = o * outer_stride + c;
+  const bool has_b = valid && (c + 1 < n_inner);
+  auto at = [sm, cl](int l, int pos) -> C& {
+    const int sw = (__popc(pos & 31) & 1) ? CP : 0;
+    return sm[pos * LW + ((l * CP + cl) ^ sw)];
+  };
+  C v[2][16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int p = t + r * T;
+    R a = 0, b = 0;
+    if (valid && p < n) {
+      const long long idx = base + p * axis_stride;
+      a = x[idx];
+      if (has_b) b = x[idx + 1];
+    }
+    v[0][r] = mk<C>(a, b);
+    v[1][r] = p < n ? cmul(v[0][r], __ldg(&tw2[p])) : mk<C>(0, 0);
+  }
+  rf_forward<R, L, 2>(v, t, twL, at);
+#pragma unroll
+  for (int idx = 0; idx < 16; ++idx) {
+    const int k = rf_freq<L>(t, idx);
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      C w = __ldg(&sym[l * L + k]);
+      if (conj_sym) w.y = -w.y;
+      v[l][idx] = cmul(v[l][idx], w);
+    }
+  }
+  rf_inverse<R, L, 2>(v, t, twL, at);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int p = t + r * T;
+    if (valid && p < n) {
+      const C res = cadd(v[0][r], cmul(v[1][r], cconj(__ldg(&tw2[p]))));
+      const long long idx = base + p * axis_stride;
+      const int ts = E.t_is_axis ? p : (int)o;
+      axis_store(E, idx, ts, res.x);
+      if (has_b) axis_store(E, idx + 1, ts, res.y);
+    }
+  }
+}
+
+template <typename R> constexpr int rows_nt() { return 256; }
+template <typename R> constexpr int axis_nt() { return sizeof(R) == 4 ? 512 : 256; }
+
+template <typename R, int L>
+static cudaError_t launch_rows_reg_L(fde_problem* P, const R* x, R* out, int conj_sym, const cplx<R>* sym,
+                                     const AxisTables<R>& T, cudaStream_t st) {
+  constexpr int NT = rows_nt<R>();
+  constexpr int PAIRS = NT / (L / 16);
+  const long long nrows = (long long)P->nt * P->nx;
+  const long long npairs = (nrows + 1) / 2;
+  const long long grid = (npairs + PAIRS - 1) / PAIRS;
+  const size_t smem = (size_t)PAIRS * 2 * (L + L / 16) * sizeof(cplx<R>);
+  k_rows_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(x, out, nrows, P->ax[2].n, sym, T.tw2, T.twL, conj_sym);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename R, int L>
+static cudaError_t launch_axis_reg_L(const R* x, int n, long long axis_stride, long long n_inner,
+                                     long long outer_stride, long long n_outer, const cplx<R>* sym,
+                                     const AxisTables<R>& T, int conj_sym, const AxisEpi<R>& E, cudaStream_t st) {
+  constexpr int NT = axis_nt<R>();
+  constexpr int CP = NT / (L / 16);
+  const long long total = n_outer * ((n_inner + 1) / 2);
+  const long long grid = (total + CP - 1) / CP;
+  const size_t smem = (size_t)L * 2 * CP * sizeof(cplx<R>);
+  k_axis_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym,
+                                                         T.tw2, T.twL, conj_sym, E);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+#define FDE_FOR_EACH_L(M) M(16) M(32) M(64) M(128) M(256) M(512) M(1024) M(2048) M(4096)
+
+template <typename R>
+cudaError_t launch_rows_reg(fde_problem* P, const R* x, R* out, int conj_sym, const cplx<R>* sym,
+                            const AxisTables<R>& T, cudaStream_t st) {
+  switch (P->ax[2].L) {
+#define FDE_CASE(LL) \
+  case LL: return launch_rows_reg_L<R, LL>(P, x, out, conj_sym, sym, T, st);
+    FDE_FOR_EACH_L(FDE_CASE)
+#undef FDE_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename R>
+cudaError_t launch_axis_reg(int L, const R* x, int n, long long axis_stride, long long n_inner,
+                            long long outer_stride, long long n_outer, const cplx<R>* sym, const AxisTables<R>& T,
+                            int conj_sym, const AxisEpi<R>& E, cudaStream_t st) {
+  switch (L) {
+#define FDE_CASE(LL)                                                                                       \
+  case LL:                                                                                                 \
+    return launch_axis_reg_L<R, LL>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym, E, \
+                                    st);
+    FDE_FOR_EACH_L(FDE_CASE)
+#undef FDE_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_rows_reg<double>(fde_problem*, const double*, double*, int, const double2*,
+                                             const AxisTables<double>&, cudaStream_t);
+template cudaError_t launch_rows_reg<float>(fde_problem*, const float*, float*, int, const float2*,
+                                            const AxisTables<float>&, cudaStream_t);
+template cudaError_t launch_axis_reg<double>(int, const double*, int, long long, long long, long long, long long,
+                                             const double2*, const AxisTables<double>&, int,
+                                             const AxisEpi<double>&, cudaStream_t);
+template cudaError_t launch_axis_reg<float>(int, const float*, int, long long, long long, long long, long long,
+                                            const float2*, const AxisTables<float>&, int, const AxisEpi<float>&,
+                                            cudaStream_t);
+
+template <typename R>
+static cudaError_t set_attrs_reg() {
+  const int big = 200 * 1024;
+  cudaError_t e = cudaSuccess;
+#define FDE_ATTR(LL)                                                                                        \
+  if (e == cudaSuccess)                                                                                     \
+    e = cudaFuncSetAttribute(k_rows_reg<R, LL, rows_nt<R>()>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
+  if (e == cudaSuccess)                                                                                     \
+    e = cudaFuncSetAttribute(k_axis_reg<R, LL, axis_nt<R>()>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  FDE_FOR_EACH_L(FDE_ATTR)
+#undef FDE_ATTR
+  return e;
+}
+
+cudaError_t toeplitz_reg_set_smem_attrs() {
+  cudaError_t e = set_attrs_reg<float>();
+  if (e != cudaSuccess) return e;
+  return set_attrs_reg<double>();
+}
+
 }  // namespace fde
