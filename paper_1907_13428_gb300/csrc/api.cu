@@ -178,11 +178,16 @@ struct SolveInfo {
   double relres = 0.0;
 };
 
-// Solve S y = rhs, y holding a warm start. FP64: PCG in double. MIXED: double
-// iterative refinement around float PCG on the correction.
-int subsolve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const double* rhs, double* y, double tol,
-             cudaStream_t st, SolveInfo* info) {
+// Solve S y = rhs, y holding a warm start, with rhs = c + B^T q.
+// FP64: PCG in double on rhs (formed by the caller). MIXED: double iterative
+// refinement around float PCG on the correction; each residual is evaluated in
+// the folded form rhs - S y = (c - M1 y) + B^T (q - M2^-1 B y), one double B and
+// one double B^T, and leaves B y of the returned y in V_BY (by_valid = true).
+// The norm of rhs, used only for the relative stopping test, is formed in float.
+int subsolve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const double* rhs, const double* c,
+             const double* q, double* y, double tol, cudaStream_t st, SolveInfo* info, bool* by_valid) {
   const long long N = P->N;
+  *by_valid = false;
   if (o->precision == FDE_FP64) {
     auto A = [&](const double* x, double* out) { return op_S<double>(P, dg, x, out, scratch64(P), st); };
     auto M = [&](const double* r, double* z) { return op_M<double>(P, dg, r, z, st); };
@@ -195,8 +200,15 @@ int subsolve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const doub
     info->relres = rel;
     return s;
   }
-  // mixed
-  CK((dot<double, double>(P, rhs, rhs, N, S_TMP0, FIN_STORE, st)));
+  // mixed: ||rhs||^2 from a float evaluation of c + B^T q
+  const long long last = (long long)(P->nt - 1) * P->nx * P->ny;
+  const SliceDiag one{{1.0, 1.0}};
+  auto s32 = scratch32(P);
+  auto s64 = scratch64(P);
+  CK(to_f32(q, P->v32[F_B], N, st));
+  CK(to_f32(c, P->v32[F_R], N, st));
+  CK(apply_B<float>(P, 1, P->v32[F_B], P->v32[F_Z], nullptr, P->v32[F_R], &one, s32.t1, s32.t2, st));
+  CK((dot<float, float>(P, P->v32[F_Z], P->v32[F_Z], N, S_TMP0, FIN_STORE, st)));
   int flag = read_scalars(P, st);
   if (flag < 0) return flag;
   const double bb = P->hscal[S_TMP0];
@@ -207,12 +219,15 @@ int subsolve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const doub
   }
   const double inner = o->inner_tol_mixed > 0 ? o->inner_tol_mixed : 1e-4;
   const int maxref = o->max_refine > 0 ? o->max_refine : 20;
-  auto A32 = [&](const float* x, float* out) { return op_S<float>(P, dg, x, out, scratch32(P), st); };
+  auto A32 = [&](const float* x, float* out) { return op_S<float>(P, dg, x, out, s32, st); };
   auto M32 = [&](const float* r, float* z) { return op_M<float>(P, dg, r, z, st); };
   for (int k = 0; k <= maxref; ++k) {
-    RK(op_S<double>(P, dg, y, P->v64[V_SD], scratch64(P), st));
+    CK(apply_B<double>(P, 0, y, P->v64[V_BY], nullptr, nullptr, nullptr, s64.t1, s64.t2, st));
+    CK(fold(P->v64[V_BY], q, c, y, dg.M2inv.v, dg.M1.v, last, N, P->v64[V_SD], P->v64[V_Z], st));
+    CK(apply_B<double>(P, 1, P->v64[V_SD], P->v64[V_R], nullptr, P->v64[V_Z], &one, s64.t1, s64.t2, st));
     info->fp64_matvecs += 2;
-    CK(residual(P, rhs, P->v64[V_SD], P->v64[V_R], N, S_RR, st));
+    *by_valid = true;
+    CK((dot<double, double>(P, P->v64[V_R], P->v64[V_R], N, S_RR, FIN_STORE, st)));
     flag = read_scalars(P, st);
     if (flag < 0) return flag;
     const double rel = std::sqrt(P->hscal[S_RR] / bb);
@@ -229,6 +244,7 @@ int subsolve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const doub
     info->refine += 1;
     if (s != FDE_OK && s != FDE_ENOCONV) return s;
     CK(add_f32(y, P->v32[F_X], N, st));
+    *by_valid = false;
   }
   return FDE_ENOCONV;
 }
@@ -430,9 +446,11 @@ int fde_admm_solve(fde_problem* P, const fde_admm_opts* o, const double* ybar, c
   const SliceDiag one{{1.0, 1.0}};
   for (int j = 0; j < o->max_admm; ++j) {
     CK(admm_pre(A, P->v64[V_C], P->v64[V_BU], P->v64[V_R0], P->v64[V_Q], st));
-    // rhs = c + B^T q
-    CK(apply_B<double>(P, 1, P->v64[V_Q], P->v64[V_RHS], nullptr, P->v64[V_C], &one, s64.t1, s64.t2, st));
-    info.fp64_matvecs += 1;
+    if (o->precision == FDE_FP64) {
+      // rhs = c + B^T q
+      CK(apply_B<double>(P, 1, P->v64[V_Q], P->v64[V_RHS], nullptr, P->v64[V_C], &one, s64.t1, s64.t2, st));
+      info.fp64_matvecs += 1;
+    }
     double tol;
     if (o->inner_tol_mode == 1) {
       tol = o->inner_tol;
@@ -440,14 +458,17 @@ int fde_admm_solve(fde_problem* P, const fde_admm_opts* o, const double* ybar, c
       const double mn = std::fmin(res[0], std::fmin(res[1], res[2]));
       tol = 0.05 * std::fmax(mn, o->tol_admm);
     }
-    const int s = subsolve(P, dg, o, P->v64[V_RHS], Y, tol, st, &info);
+    bool by_valid = false;
+    const int s = subsolve(P, dg, o, P->v64[V_RHS], P->v64[V_C], P->v64[V_Q], Y, tol, st, &info, &by_valid);
     if (s != FDE_OK && s != FDE_ENOCONV) {
       status = s;
       break;
     }
     S.max_sub_relres = std::fmax(S.max_sub_relres, info.relres);
-    CK(apply_B<double>(P, 0, Y, P->v64[V_BY], nullptr, nullptr, nullptr, s64.t1, s64.t2, st));
-    info.fp64_matvecs += 1;
+    if (!by_valid) {
+      CK(apply_B<double>(P, 0, Y, P->v64[V_BY], nullptr, nullptr, nullptr, s64.t1, s64.t2, st));
+      info.fp64_matvecs += 1;
+    }
     RK(clear_flag(P, st));
     CK(admm_post(P, A, Y, P->v64[V_BY], P->v64[V_BU], P->v64[V_R0], U, st));
     const int flag = read_scalars(P, st);

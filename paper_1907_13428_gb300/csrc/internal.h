@@ -20,6 +20,8 @@ template <typename R> struct AxisTables {
   cplx<R>* twL = nullptr;  // W_L^m, m in [0, L): FFT table of the embedding length
   cplx<R>* lam = nullptr;  // T. Chan circulant eigenvalues, length n (unscaled)
   cplx<R>* twn = nullptr;  // W_n^m, m in [0, n): FFT table of the exact length
+  cplx<R>* symD = nullptr; // [2][L]: x1 axis, implicit Euler: sym + (psi/h_t)/(2L), i.e. the
+                           //         symbol of X shifted by the diagonal that carries +psi/h_t x_t
   cplx<R>* symL = nullptr; // [2][L]: embedding symbol halves of the one-sided L alone,
                            //         scaled by 1/(2L) (space axes, double only; gradient)
 };

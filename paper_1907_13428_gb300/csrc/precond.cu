@@ -133,11 +133,11 @@ __global__ void __launch_bounds__(1024) k_prec_axis(cplx<R>* __restrict__ spec, 
       const int i = (int)(c / dv.Hp), j = (int)(c - (long long)i * dv.Hp);
       if (j >= dv.H) continue;  // padding column: stays zero
       const C a = __ldg(&lt[k]), b = __ldg(&lx[i]), d = __ldg(&ly[j]);
-      const double lr = dv.psi * ((double)a.x - (double)b.x - (double)d.x);
-      const double li = dv.psi * ((double)a.y - (double)b.y - (double)d.y);
-      const double mag = lr * lr + li * li;
-      const double sigma = dv.adjoint ? mag : dv.m1 + mag * dv.inv_m2;
-      const R s = (R)(dv.inv_N / sigma);
+      const R lr = (R)dv.psi * (a.x - b.x - d.x);
+      const R li = (R)dv.psi * (a.y - b.y - d.y);
+      const R mag = lr * lr + li * li;
+      const R sigma = dv.adjoint ? mag : (R)dv.m1 + mag * (R)dv.inv_m2;
+      const R s = (R)dv.inv_N / sigma;
       buf[e] = cscale(buf[e], s);
     }
     __syncthreads();
@@ -158,6 +158,10 @@ cudaError_t launch_prec_axis_reg(int L, cplx<R>* spec, long long axis_stride, lo
                                  const DivArgs& dv, const cplx<R>* lt, const cplx<R>* lx, const cplx<R>* ly,
                                  cudaStream_t st);
 cudaError_t precond_reg_set_smem_attrs();
+template <typename R>
+cudaError_t launch_prec_rows_reg(int L, int inverse, const R* r, R* z, cplx<R>* spec, long long nrows, int H, int Hp,
+                                 const cplx<R>* twn, cudaStream_t st);
+cudaError_t precond_rows_reg_set_smem_attrs();
 
 template <typename R>
 cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const R* r, R* z, cplx<R>* spec,
@@ -169,8 +173,12 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
   const long long nrows = (long long)P->nt * P->nx;
   const int ny = P->ny, H = P->H, Hp = P->Hp;
   cudaError_t err;
+  const bool rows_pow2 = ny >= 16 && (ny & (ny - 1)) == 0;
   // 1. rows forward
-  {
+  if (rows_pow2) {
+    if ((err = launch_prec_rows_reg<R>(ny, 0, r, nullptr, spec, nrows, H, Hp, ptables<R>(Ay).twn, st)) != cudaSuccess)
+      return err;
+  } else {
     const int threads = (ny > kPEPT * 256) ? 512 : 256;
     int pairs = (kPEPT * threads) / ny;
     if (pairs < 1) pairs = 1;
@@ -233,7 +241,10 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   // 5. rows inverse
-  {
+  if (rows_pow2) {
+    if ((err = launch_prec_rows_reg<R>(ny, 1, nullptr, z, spec, nrows, H, Hp, ptables<R>(Ay).twn, st)) != cudaSuccess)
+      return err;
+  } else {
     const int threads2 = (ny > kPEPT * 256) ? 512 : 256;
     int pairs = (kPEPT * threads2) / ny;
     if (pairs < 1) pairs = 1;
@@ -269,7 +280,8 @@ cudaError_t precond_set_smem_attrs() {
   if (e) return e;
   e = cudaFuncSetAttribute(k_prec_axis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e) return e;
-  return precond_reg_set_smem_attrs();
+  if ((e = precond_reg_set_smem_attrs())) return e;
+  return precond_rows_reg_set_smem_attrs();
 }
 
 }  // namespace fde
@@ -331,12 +343,14 @@ __global__ void __launch_bounds__(NT) k_prec_axis_reg(cplx<R>* __restrict__ spec
 #pragma unroll
       for (int idx = 0; idx < 16; ++idx) {
         const int k = rf_freq<L>(t, idx);
+        // sigma in the arithmetic of the transform (float on the float path:
+        // double divides would run at 1/58 of the float rate)
         const C a = __ldg(&lt[k]);
-        const double lr = dv.psi * ((double)a.x - (double)b.x - (double)d.x);
-        const double li = dv.psi * ((double)a.y - (double)b.y - (double)d.y);
-        const double mag = lr * lr + li * li;
-        const double sigma = dv.adjoint ? mag : dv.m1 + mag * dv.inv_m2;
-        const R sc = pad ? (R)0 : (R)(dv.inv_N / sigma);
+        const R lr = (R)dv.psi * (a.x - b.x - d.x);
+        const R li = (R)dv.psi * (a.y - b.y - d.y);
+        const R mag = lr * lr + li * li;
+        const R sigma = dv.adjoint ? mag : (R)dv.m1 + mag * (R)dv.inv_m2;
+        const R sc = pad ? (R)0 : (R)dv.inv_N / sigma;
         v[0][idx] = cscale(v[0][idx], sc);
       }
       rf_inverse<R, L, 1>(v, t, twn, at);
@@ -405,6 +419,140 @@ cudaError_t precond_reg_set_smem_attrs() {
   if (e == cudaSuccess)                                                                           \
     e = cudaFuncSetAttribute(k_prec_axis_reg<double, LL, prec_nt<double>()>,                      \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  FDE_FOR_EACH_PL(FDE_ATTR)
+#undef FDE_ATTR
+  return e;
+}
+
+}  // namespace fde
+
+// ===========================================================================
+// Register-resident x2-row transforms of the preconditioner (power-of-two
+// ny >= 16). Two real rows a, b form the complex line a + i b; the half
+// spectra are A_k = (Z_k + conj Z_{n-k})/2 and B_k = (Z_k - conj Z_{n-k})/(2i).
+// ===========================================================================
+namespace fde {
+
+template <typename R, int L, int NT>
+__global__ void __launch_bounds__(NT) k_prec_rows_fwd_reg(const R* __restrict__ r, cplx<R>* __restrict__ spec,
+                                                           long long nrows, int H, int Hp,
+                                                           const cplx<R>* __restrict__ twn) {
+  using C = cplx<R>;
+  constexpr int T = L / 16, PAIRS = NT / T, LS = L + L / 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int pr = threadIdx.x / T, t = threadIdx.x - pr * T;
+  const long long ra = ((long long)blockIdx.x * PAIRS + pr) * 2, rb = ra + 1;
+  C* my = sm + pr * LS;
+  auto at = [my](int, int pos) -> C& { return my[pos + (pos >> 4)]; };
+  C v[1][16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int p = t + q * T;
+    v[0][q] = mk<C>(ra < nrows ? r[ra * L + p] : (R)0, rb < nrows ? r[rb * L + p] : (R)0);
+  }
+  rf_forward<R, L, 1>(v, t, twn, at);
+#pragma unroll
+  for (int idx = 0; idx < 16; ++idx) at(0, rf_freq<L>(t, idx)) = v[0][idx];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int k = t + q * T;
+    if (k < H) {
+      const C zk = at(0, k);
+      const C zm = cconj(at(0, k == 0 ? 0 : L - k));
+      const C A = mk<C>((zk.x + zm.x) * (R)0.5, (zk.y + zm.y) * (R)0.5);
+      const C B = mk<C>((zk.y - zm.y) * (R)0.5, -(zk.x - zm.x) * (R)0.5);
+      if (ra < nrows) spec[ra * Hp + k] = A;
+      if (rb < nrows) spec[rb * Hp + k] = B;
+    }
+  }
+}
+
+template <typename R, int L, int NT>
+__global__ void __launch_bounds__(NT) k_prec_rows_inv_reg(const cplx<R>* __restrict__ spec, R* __restrict__ z,
+                                                           long long nrows, int H, int Hp,
+                                                           const cplx<R>* __restrict__ twn) {
+  using C = cplx<R>;
+  constexpr int T = L / 16, PAIRS = NT / T, LS = L + L / 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int pr = threadIdx.x / T, t = threadIdx.x - pr * T;
+  const long long ra = ((long long)blockIdx.x * PAIRS + pr) * 2, rb = ra + 1;
+  C* my = sm + pr * LS;
+  auto at = [my](int, int pos) -> C& { return my[pos + (pos >> 4)]; };
+  C v[1][16];
+#pragma unroll
+  for (int idx = 0; idx < 16; ++idx) {
+    const int k = rf_freq<L>(t, idx);
+    const bool lo = k < H;
+    const int kk = lo ? k : L - k;
+    C A = ra < nrows ? spec[ra * Hp + kk] : mk<C>(0, 0);
+    C B = rb < nrows ? spec[rb * Hp + kk] : mk<C>(0, 0);
+    if (!lo) {
+      A = cconj(A);
+      B = cconj(B);
+    }
+    v[0][idx] = mk<C>(A.x - B.y, A.y + B.x);  // A + i B
+  }
+  rf_inverse<R, L, 1>(v, t, twn, at);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int p = t + q * T;
+    if (ra < nrows) z[ra * L + p] = v[0][q].x;
+    if (rb < nrows) z[rb * L + p] = v[0][q].y;
+  }
+}
+
+template <typename R, int L>
+static cudaError_t launch_prec_rows_reg_L(int inverse, const R* r, R* z, cplx<R>* spec, long long nrows, int H,
+                                          int Hp, const cplx<R>* twn, cudaStream_t st) {
+  constexpr int NT = 256;
+  constexpr int PAIRS = NT / (L / 16);
+  const long long npairs = (nrows + 1) / 2;
+  const long long grid = (npairs + PAIRS - 1) / PAIRS;
+  const size_t smem = (size_t)PAIRS * (L + L / 16) * sizeof(cplx<R>);
+  if (inverse)
+    k_prec_rows_inv_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(spec, z, nrows, H, Hp, twn);
+  else
+    k_prec_rows_fwd_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(r, spec, nrows, H, Hp, twn);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_prec_rows_reg(int L, int inverse, const R* r, R* z, cplx<R>* spec, long long nrows, int H, int Hp,
+                                 const cplx<R>* twn, cudaStream_t st) {
+  switch (L) {
+#define FDE_CASE(LL) \
+  case LL: return launch_prec_rows_reg_L<R, LL>(inverse, r, z, spec, nrows, H, Hp, twn, st);
+    FDE_FOR_EACH_PL(FDE_CASE)
+#undef FDE_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_prec_rows_reg<float>(int, int, const float*, float*, float2*, long long, int, int,
+                                                 const float2*, cudaStream_t);
+template cudaError_t launch_prec_rows_reg<double>(int, int, const double*, double*, double2*, long long, int, int,
+                                                  const double2*, cudaStream_t);
+
+cudaError_t precond_rows_reg_set_smem_attrs() {
+  const int big = 200 * 1024;
+  cudaError_t e = cudaSuccess;
+#define FDE_ATTR(LL)                                                                                            \
+  if (e == cudaSuccess)                                                                                         \
+    e = cudaFuncSetAttribute(k_prec_rows_fwd_reg<float, LL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                             big);                                                                              \
+  if (e == cudaSuccess)                                                                                         \
+    e = cudaFuncSetAttribute(k_prec_rows_inv_reg<float, LL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                             big);                                                                              \
+  if (e == cudaSuccess)                                                                                         \
+    e = cudaFuncSetAttribute(k_prec_rows_fwd_reg<double, LL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             big);                                                                              \
+  if (e == cudaSuccess)                                                                                         \
+    e = cudaFuncSetAttribute(k_prec_rows_inv_reg<double, LL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             big);
   FDE_FOR_EACH_PL(FDE_ATTR)
 #undef FDE_ATTR
   return e;

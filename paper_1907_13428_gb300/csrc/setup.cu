@@ -94,6 +94,13 @@ __global__ void k_halves(const double2* __restrict__ lam, int L, double2* __rest
   }
 }
 
+// out[e] = in[e] + (d, 0): adds a real constant to every symbol entry (a
+// diagonal shift of the Toeplitz factor).
+__global__ void k_shift(const double2* __restrict__ in, double d, double2* __restrict__ out, int n) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+    out[e] = make_double2(in[e].x + d, in[e].y);
+}
+
 __global__ void k_to_float2(const double2* __restrict__ in, float2* __restrict__ out, int n) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
     out[e] = make_float2((float)in[e].x, (float)in[e].y);
@@ -211,6 +218,17 @@ cudaError_t setup_axis_tables(fde_problem* P, cudaStream_t st) {
   note_launches(1);
     k_halves<<<(2 * L + 255) / 256, 256, 0, st>>>(lamL, L, A.d.symL);
   note_launches(1);
+    if (axis == 1 && P->euler) {
+      // +psi/h_t x_t of the implicit-Euler term as a diagonal shift of the x1 factor
+      if ((e = fde_alloc(P, &p, sizeof(double2) * 2 * L))) return e;
+      A.d.symD = (double2*)p;
+      if ((e = fde_alloc(P, &p, sizeof(float2) * 2 * L))) return e;
+      A.f.symD = (float2*)p;
+      k_shift<<<(2 * L + 255) / 256, 256, 0, st>>>(A.d.sym, (P->psi / P->ht) / (2.0 * L), A.d.symD, 2 * L);
+      note_launches(1);
+      k_to_float2<<<(2 * L + 255) / 256, 256, 0, st>>>(A.d.symD, A.f.symD, 2 * L);
+      note_launches(1);
+    }
     // T. Chan eigenvalues of order n
     k_dft<<<(n + 127) / 128, 128, 0, st>>>(tch, n, A.d.twn, A.d.lam, 1.0);
   note_launches(1);

@@ -25,15 +25,97 @@ namespace fde {
 
 constexpr int kEPT = 16;  // complex elements staged per thread in an FFT pass
 
+// Epilogue of a pass, per output element idx on time slice t:
+//   out = dsc(t) * (acc[idx] + res + ct * (xt[idx] - xt[idx -/+ plane])) + addc(t) * addv[idx]
+// with dsc/addc taking v0 on slices 0..nt-2 and v1 on the last slice.
+template <typename R> struct AxisEpi {
+  R* out;
+  const R* acc;   // nullable
+  const R* xt;    // nullable: time-difference term source
+  int tdir;       // +1: x_t - x_{t-1} (B), -1: x_t - x_{t+1} (B^T)
+  R ct;           // psi / h_t
+  long long plane;
+  int nt;
+  int t_is_axis;  // strided passes: 1: time index = position along the axis; 0: = outer index
+  long long rows_per_slice;  // x2 pass: time index = row / rows_per_slice (= nx)
+  int plain;      // 1: out = res only (no acc, time term, diagonal or addend)
+  int nb_only;    // 1: time term is -ct xt[idx -/+ plane] only (+ct x_t is in the x1 symbol)
+  int has_dsc;
+  R dsc0, dsc1;
+  const R* addv;  // nullable
+  R addc0, addc1;
+};
+
+template <typename R>
+__device__ __forceinline__ void axis_store(const AxisEpi<R>& E, long long idx, int t, R res) {
+  if (E.plain) {
+    E.out[idx] = res;
+    return;
+  }
+  R v = res;
+  if (E.acc) v += E.acc[idx];
+  if (E.xt) {
+    R nb = 0;
+    if (E.tdir > 0) {
+      if (t > 0) nb = E.xt[idx - E.plane];
+    } else {
+      if (t < E.nt - 1) nb = E.xt[idx + E.plane];
+    }
+    v += E.nb_only ? -E.ct * nb : E.ct * (E.xt[idx] - nb);
+  }
+  const bool last = (t == E.nt - 1);
+  if (E.has_dsc) v *= last ? E.dsc1 : E.dsc0;
+  if (E.addv) v += (last ? E.addc1 : E.addc0) * E.addv[idx];
+  E.out[idx] = v;
+}
+
+
+// Two-phase form of axis_store for batching the epilogue's loads: epi_load
+// fetches the operands of one element, epi_finish combines and stores.
+template <typename R> struct EpiIn {
+  R acc, x0, xn, add;
+};
+
+template <typename R>
+__device__ __forceinline__ EpiIn<R> epi_load(const AxisEpi<R>& E, long long idx, int t) {
+  EpiIn<R> in{0, 0, 0, 0};
+  if (E.plain) return in;
+  if (E.acc) in.acc = E.acc[idx];
+  if (E.xt) {
+    if (!E.nb_only) in.x0 = E.xt[idx];
+    if (E.tdir > 0) {
+      if (t > 0) in.xn = E.xt[idx - E.plane];
+    } else {
+      if (t < E.nt - 1) in.xn = E.xt[idx + E.plane];
+    }
+  }
+  if (E.addv) in.add = E.addv[idx];
+  return in;
+}
+
+template <typename R>
+__device__ __forceinline__ void epi_finish(const AxisEpi<R>& E, const EpiIn<R>& in, long long idx, int t, R res) {
+  if (E.plain) {
+    E.out[idx] = res;
+    return;
+  }
+  R v = res + in.acc;
+  if (E.xt) v += E.nb_only ? -E.ct * in.xn : E.ct * (in.x0 - in.xn);
+  const bool last = (t == E.nt - 1);
+  if (E.has_dsc) v *= last ? E.dsc1 : E.dsc0;
+  if (E.addv) v += (last ? E.addc1 : E.addc0) * in.add;
+  E.out[idx] = v;
+}
+
 // ---------------------------------------------------------------------------
 // x2 axis: rows of n contiguous values; a CTA takes `pairs` row pairs and
 // builds 2*pairs complex lines of length L (pair p, half s -> line 2p+s).
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(512) k_rows(const R* __restrict__ x, R* __restrict__ out, long long nrows,
-                                               int n, int L, const cplx<R>* __restrict__ sym,
-                                               const cplx<R>* __restrict__ tw2, const cplx<R>* __restrict__ twL,
-                                               FftPlan pl, int conj_sym, int pairs) {
+__global__ void __launch_bounds__(512) k_rows(const R* __restrict__ x, long long nrows, int n, int L,
+                                               const cplx<R>* __restrict__ sym, const cplx<R>* __restrict__ tw2,
+                                               const cplx<R>* __restrict__ twL, FftPlan pl, int conj_sym, int pairs,
+                                               AxisEpi<R> E) {
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -65,46 +147,9 @@ __global__ void __launch_bounds__(512) k_rows(const R* __restrict__ x, R* __rest
     const int p = e / n, j = e - p * n;
     const long long ra = row0 + 2 * p, rb = ra + 1;
     const C v = cadd(buf[(2 * p) * L + j], cmul(buf[(2 * p + 1) * L + j], cconj(__ldg(&tw2[j]))));
-    if (ra < nrows) out[ra * n + j] = v.x;
-    if (rb < nrows) out[rb * n + j] = v.y;
+    if (ra < nrows) axis_store(E, ra * n + j, (int)(ra / E.rows_per_slice), v.x);
+    if (rb < nrows) axis_store(E, rb * n + j, (int)(rb / E.rows_per_slice), v.y);
   }
-}
-
-// Epilogue of a strided-axis pass, per output element idx on time slice t:
-//   out = dsc(t) * (acc[idx] + res + ct * (xt[idx] - xt[idx -/+ plane])) + addc(t) * addv[idx]
-// with dsc/addc taking v0 on slices 0..nt-2 and v1 on the last slice.
-template <typename R> struct AxisEpi {
-  R* out;
-  const R* acc;   // nullable
-  const R* xt;    // nullable: time-difference term source
-  int tdir;       // +1: x_t - x_{t-1} (B), -1: x_t - x_{t+1} (B^T)
-  R ct;           // psi / h_t
-  long long plane;
-  int nt;
-  int t_is_axis;  // 1: time index = position along the axis; 0: = outer index
-  int has_dsc;
-  R dsc0, dsc1;
-  const R* addv;  // nullable
-  R addc0, addc1;
-};
-
-template <typename R>
-__device__ __forceinline__ void axis_store(const AxisEpi<R>& E, long long idx, int t, R res) {
-  R v = res;
-  if (E.acc) v += E.acc[idx];
-  if (E.xt) {
-    R nb = 0;
-    if (E.tdir > 0) {
-      if (t > 0) nb = E.xt[idx - E.plane];
-    } else {
-      if (t < E.nt - 1) nb = E.xt[idx + E.plane];
-    }
-    v += E.ct * (E.xt[idx] - nb);
-  }
-  const bool last = (t == E.nt - 1);
-  if (E.has_dsc) v *= last ? E.dsc1 : E.dsc0;
-  if (E.addv) v += (last ? E.addc1 : E.addc0) * E.addv[idx];
-  E.out[idx] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -164,8 +209,8 @@ __global__ void __launch_bounds__(1024) k_axis(const R* __restrict__ x, int n, i
 
 // Register-resident variants (defined below) used for power-of-two L >= 16.
 template <typename R>
-cudaError_t launch_rows_reg(fde_problem* P, const R* x, R* out, int conj_sym, const cplx<R>* sym,
-                            const AxisTables<R>& T, cudaStream_t st);
+cudaError_t launch_rows_reg(fde_problem* P, const R* x, int conj_sym, const cplx<R>* sym, const AxisTables<R>& T,
+                            const AxisEpi<R>& E, cudaStream_t st);
 template <typename R>
 cudaError_t launch_axis_reg(int L, const R* x, int n, long long axis_stride, long long n_inner,
                             long long outer_stride, long long n_outer, const cplx<R>* sym, const AxisTables<R>& T,
@@ -179,12 +224,12 @@ template <> const AxisTables<float>& tables<float>(const Axis& A) { return A.f; 
 template <typename R> static int rows_threads(int L) { return (2 * L > kEPT * 256) ? 512 : 256; }
 
 template <typename R>
-static cudaError_t launch_rows(fde_problem* P, const R* x, R* out, int conj_sym, const cplx<R>* sym,
+static cudaError_t launch_rows(fde_problem* P, const R* x, int conj_sym, const cplx<R>* sym, const AxisEpi<R>& E,
                                cudaStream_t st) {
   const Axis& A = P->ax[2];
   const AxisTables<R>& T = tables<R>(A);
   const int L = A.L;
-  if (L >= 16) return launch_rows_reg<R>(P, x, out, conj_sym, sym ? sym : T.sym, T, st);
+  if (L >= 16) return launch_rows_reg<R>(P, x, conj_sym, sym ? sym : T.sym, T, E, st);
   const int threads = rows_threads<R>(L);
   const int cap = kEPT * threads;  // complex elements per CTA
   int pairs = cap / (2 * L);
@@ -194,8 +239,8 @@ static cudaError_t launch_rows(fde_problem* P, const R* x, R* out, int conj_sym,
   if (pairs > npairs) pairs = (int)npairs;
   const long long grid = (npairs + pairs - 1) / pairs;
   const size_t smem = (size_t)2 * pairs * L * sizeof(cplx<R>);
-  k_rows<R><<<(unsigned)grid, threads, smem, st>>>(x, out, nrows, A.n, L, sym ? sym : T.sym, T.tw2, T.twL,
-                                                   A.planL, conj_sym, pairs);
+  k_rows<R><<<(unsigned)grid, threads, smem, st>>>(x, nrows, A.n, L, sym ? sym : T.sym, T.tw2, T.twL, A.planL,
+                                                   conj_sym, pairs, E);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -238,7 +283,16 @@ static cudaError_t launch_axis(fde_problem* P, int axis, const R* x, int conj_sy
 template <typename R>
 cudaError_t apply_B(fde_problem* P, int transpose, const R* x, R* y, const SliceDiag* dscale, const R* addv,
                     const SliceDiag* addc, R* tmp1, R* tmp2, cudaStream_t st) {
-  cudaError_t err = launch_rows<R>(P, x, tmp1, transpose, nullptr, st);
+  // x1 pass first (plain store), then the optional time pass, then the x2 pass,
+  // whose coalesced epilogue adds the partial results, the implicit-Euler time
+  // term, the per-slice diagonal and the addend.
+  AxisEpi<R> Ex{};
+  Ex.out = tmp1;
+  Ex.nt = P->nt;
+  Ex.plain = 1;
+  // implicit Euler: the x1 symbol shifted by psi/h_t also adds +psi/h_t x_t
+  const cplx<R>* symD = P->euler ? tables<R>(P->ax[1]).symD : nullptr;
+  cudaError_t err = launch_axis<R>(P, 1, x, transpose, symD, Ex, st);
   if (err != cudaSuccess) return err;
   const R* acc = tmp1;
   if (!P->euler) {
@@ -256,11 +310,12 @@ cudaError_t apply_B(fde_problem* P, int transpose, const R* x, R* y, const Slice
   E.acc = acc;
   E.nt = P->nt;
   E.plane = (long long)P->nx * P->ny;
-  E.t_is_axis = 0;
+  E.rows_per_slice = P->nx;
   if (P->euler) {
     E.xt = x;
     E.tdir = transpose ? -1 : 1;
     E.ct = (R)(P->psi / P->ht);
+    E.nb_only = symD != nullptr;
   }
   if (dscale) {
     E.has_dsc = 1;
@@ -272,7 +327,7 @@ cudaError_t apply_B(fde_problem* P, int transpose, const R* x, R* y, const Slice
     E.addc0 = (R)addc->v[0];
     E.addc1 = (R)addc->v[1];
   }
-  return launch_axis<R>(P, 1, x, transpose, nullptr, E, st);
+  return launch_rows<R>(P, x, transpose, nullptr, E, st);
 }
 
 template <typename R>
@@ -287,11 +342,13 @@ template <typename R>
 cudaError_t apply_axis_raw(fde_problem* P, int axis, const R* x, R* y, const cplx<R>* sym, int conj_sym,
                            cudaStream_t st) {
   // one spatial factor along one axis (no time term, no accumulation)
-  if (axis == 2) return launch_rows<R>(P, x, y, conj_sym, sym, st);
   AxisEpi<R> E{};
   E.out = y;
   E.nt = P->nt;
   E.plane = (long long)P->nx * P->ny;
+  E.rows_per_slice = P->nx;
+  E.plain = 1;
+  if (axis == 2) return launch_rows<R>(P, x, conj_sym, sym, E, st);
   return launch_axis<R>(P, axis, x, conj_sym, sym, E, st);
 }
 
@@ -332,10 +389,10 @@ namespace fde {
 // pair holds positions t + r T of the pair's two half-lines. Shared memory is
 // line-major with one pad element per 16 (conflict-free exchanges).
 template <typename R, int L, int NT>
-__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const R* __restrict__ x, R* __restrict__ out, long long nrows,
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const R* __restrict__ x, long long nrows,
                                                   int n, const cplx<R>* __restrict__ sym,
                                                   const cplx<R>* __restrict__ tw2, const cplx<R>* __restrict__ twL,
-                                                  int conj_sym) {
+                                                  int conj_sym, AxisEpi<R> E) {
   using C = cplx<R>;
   constexpr int T = L / 16, PAIRS = NT / T, LS = L + L / 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -368,13 +425,27 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const
     }
   }
   rf_inverse<R, L, 2>(v, t, twL, at);
+  const int ta = (int)(ra / E.rows_per_slice), tb = (int)(rb / E.rows_per_slice);
+  // epilogue in chunks of 4 positions: all operand loads of a chunk are issued
+  // before any arithmetic or store, so their latencies overlap
 #pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int p = t + r * T;
-    if (p < n) {
-      const C res = cadd(v[0][r], cmul(v[1][r], cconj(__ldg(&tw2[p]))));
-      if (ra < nrows) out[ra * n + p] = res.x;
-      if (rb < nrows) out[rb * n + p] = res.y;
+  for (int r0 = 0; r0 < 16; r0 += 4) {
+    EpiIn<R> ia[4], ib[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int p = t + (r0 + k) * T;
+      const bool ok = p < n;
+      ia[k] = (ok && ra < nrows) ? epi_load(E, ra * n + p, ta) : EpiIn<R>{0, 0, 0, 0};
+      ib[k] = (ok && rb < nrows) ? epi_load(E, rb * n + p, tb) : EpiIn<R>{0, 0, 0, 0};
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int p = t + (r0 + k) * T;
+      if (p < n) {
+        const C res = cadd(v[0][r0 + k], cmul(v[1][r0 + k], cconj(__ldg(&tw2[p]))));
+        if (ra < nrows) epi_finish(E, ia[k], ra * n + p, ta, res.x);
+        if (rb < nrows) epi_finish(E, ib[k], rb * n + p, tb, res.y);
+      }
     }
   }
 }
@@ -388,7 +459,8 @@ template <typename R, int L, int NT>
 __global__ void __launch_bounds__(NT) k_axis_reg(const R* __restrict__ x, int n, long long axis_stride,
                                                   long long n_inner, long long outer_stride, long long n_outer,
                                                   const cplx<R>* __restrict__ sym, const cplx<R>* __restrict__ tw2,
-                                                  const cplx<R>* __restrict__ twL, int conj_sym, AxisEpi<R> E) {
+                                                  const cplx<R>* __restrict__ twL, int conj_sym, AxisEpi<R> E,
+                                                  int vec2) {
   using C = cplx<R>;
   constexpr int T = L / 16, CP = NT / T, LW = 2 * CP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -413,8 +485,14 @@ __global__ void __launch_bounds__(NT) k_axis_reg(const R* __restrict__ x, int n,
     R a = 0, b = 0;
     if (valid && p < n) {
       const long long idx = base + p * axis_stride;
-      a = x[idx];
-      if (has_b) b = x[idx + 1];
+      if (vec2 && has_b) {
+        const C ab = *reinterpret_cast<const C*>(x + idx);  // (c, c+1) as one aligned vector load
+        a = ab.x;
+        b = ab.y;
+      } else {
+        a = x[idx];
+        if (has_b) b = x[idx + 1];
+      }
     }
     v[0][r] = mk<C>(a, b);
     v[1][r] = p < n ? cmul(v[0][r], __ldg(&tw2[p])) : mk<C>(0, 0);
@@ -437,6 +515,10 @@ __global__ void __launch_bounds__(NT) k_axis_reg(const R* __restrict__ x, int n,
     if (valid && p < n) {
       const C res = cadd(v[0][r], cmul(v[1][r], cconj(__ldg(&tw2[p]))));
       const long long idx = base + p * axis_stride;
+      if (E.plain && vec2 && has_b) {
+        *reinterpret_cast<C*>(E.out + idx) = res;
+        continue;
+      }
       const int ts = E.t_is_axis ? p : (int)o;
       axis_store(E, idx, ts, res.x);
       if (has_b) axis_store(E, idx + 1, ts, res.y);
@@ -448,15 +530,15 @@ template <typename R> constexpr int rows_nt() { return 256; }
 template <typename R> constexpr int axis_nt() { return sizeof(R) == 4 ? 512 : 256; }
 
 template <typename R, int L>
-static cudaError_t launch_rows_reg_L(fde_problem* P, const R* x, R* out, int conj_sym, const cplx<R>* sym,
-                                     const AxisTables<R>& T, cudaStream_t st) {
+static cudaError_t launch_rows_reg_L(fde_problem* P, const R* x, int conj_sym, const cplx<R>* sym,
+                                     const AxisTables<R>& T, const AxisEpi<R>& E, cudaStream_t st) {
   constexpr int NT = rows_nt<R>();
   constexpr int PAIRS = NT / (L / 16);
   const long long nrows = (long long)P->nt * P->nx;
   const long long npairs = (nrows + 1) / 2;
   const long long grid = (npairs + PAIRS - 1) / PAIRS;
   const size_t smem = (size_t)PAIRS * 2 * (L + L / 16) * sizeof(cplx<R>);
-  k_rows_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(x, out, nrows, P->ax[2].n, sym, T.tw2, T.twL, conj_sym);
+  k_rows_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(x, nrows, P->ax[2].n, sym, T.tw2, T.twL, conj_sym, E);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -470,8 +552,11 @@ static cudaError_t launch_axis_reg_L(const R* x, int n, long long axis_stride, l
   const long long total = n_outer * ((n_inner + 1) / 2);
   const long long grid = (total + CP - 1) / CP;
   const size_t smem = (size_t)L * 2 * CP * sizeof(cplx<R>);
+  const size_t al = 2 * sizeof(R);
+  const int vec2 = ((n_inner | axis_stride | outer_stride) & 1) == 0 && ((uintptr_t)x % al) == 0 &&
+                   ((uintptr_t)E.out % al) == 0;
   k_axis_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym,
-                                                         T.tw2, T.twL, conj_sym, E);
+                                                         T.tw2, T.twL, conj_sym, E, vec2);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -479,11 +564,11 @@ static cudaError_t launch_axis_reg_L(const R* x, int n, long long axis_stride, l
 #define FDE_FOR_EACH_L(M) M(16) M(32) M(64) M(128) M(256) M(512) M(1024) M(2048) M(4096)
 
 template <typename R>
-cudaError_t launch_rows_reg(fde_problem* P, const R* x, R* out, int conj_sym, const cplx<R>* sym,
-                            const AxisTables<R>& T, cudaStream_t st) {
+cudaError_t launch_rows_reg(fde_problem* P, const R* x, int conj_sym, const cplx<R>* sym, const AxisTables<R>& T,
+                            const AxisEpi<R>& E, cudaStream_t st) {
   switch (P->ax[2].L) {
 #define FDE_CASE(LL) \
-  case LL: return launch_rows_reg_L<R, LL>(P, x, out, conj_sym, sym, T, st);
+  case LL: return launch_rows_reg_L<R, LL>(P, x, conj_sym, sym, T, E, st);
     FDE_FOR_EACH_L(FDE_CASE)
 #undef FDE_CASE
     default: return cudaErrorInvalidValue;
@@ -505,10 +590,10 @@ cudaError_t launch_axis_reg(int L, const R* x, int n, long long axis_stride, lon
   }
 }
 
-template cudaError_t launch_rows_reg<double>(fde_problem*, const double*, double*, int, const double2*,
-                                             const AxisTables<double>&, cudaStream_t);
-template cudaError_t launch_rows_reg<float>(fde_problem*, const float*, float*, int, const float2*,
-                                            const AxisTables<float>&, cudaStream_t);
+template cudaError_t launch_rows_reg<double>(fde_problem*, const double*, int, const double2*,
+                                             const AxisTables<double>&, const AxisEpi<double>&, cudaStream_t);
+template cudaError_t launch_rows_reg<float>(fde_problem*, const float*, int, const float2*,
+                                            const AxisTables<float>&, const AxisEpi<float>&, cudaStream_t);
 template cudaError_t launch_axis_reg<double>(int, const double*, int, long long, long long, long long, long long,
                                              const double2*, const AxisTables<double>&, int,
                                              const AxisEpi<double>&, cudaStream_t);

@@ -44,15 +44,36 @@ int red_grid(long long n) {
   return (int)g;
 }
 
+// Per-thread accumulator: double for double data; for float data a
+// compensated (Kahan) float sum, converted to double once per thread, so that
+// no element pays a float->double conversion (the double pipe runs at 1/58 of
+// the float rate on this GPU) while the sum keeps close to double accuracy.
+template <typename R> struct Acc;
+template <> struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // partials[b] = sum over the grid-stride share of block b of a[i]*b[i]
 template <typename RA, typename RB>
 __global__ void __launch_bounds__(kRedThreads) k_dot(const RA* __restrict__ a, const RB* __restrict__ b, long long n,
                                                       double* __restrict__ partials) {
   __shared__ double sh[32];
-  double s = 0.0;
+  Acc<RA> acc;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    s += (double)a[i] * (double)b[i];
-  s = block_sum(s, sh);
+    acc.add(a[i] * b[i]);
+  double s = block_sum(acc.value(), sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
@@ -88,30 +109,30 @@ __global__ void __launch_bounds__(1024) k_finish(const double* __restrict__ part
   }
 }
 
-// x += alpha d; r -= alpha q; partials of r.r
+// x += alpha d; r -= alpha q; partials of r.r (arithmetic in the vectors' type)
 template <typename RV>
 __global__ void __launch_bounds__(kRedThreads) k_pcg_xr(RV* __restrict__ x, RV* __restrict__ r, const RV* __restrict__ d,
                                                          const RV* __restrict__ q, const double* __restrict__ dscal,
                                                          long long n, double* __restrict__ partials) {
   __shared__ double sh[32];
-  const double alpha = dscal[S_ALPHA];
-  double s = 0.0;
+  const RV alpha = (RV)dscal[S_ALPHA];
+  Acc<RV> acc;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    x[i] = (RV)((double)x[i] + alpha * (double)d[i]);
-    const RV ri = (RV)((double)r[i] - alpha * (double)q[i]);
+    x[i] = x[i] + alpha * d[i];
+    const RV ri = r[i] - alpha * q[i];
     r[i] = ri;
-    s += (double)ri * (double)ri;
+    acc.add(ri * ri);
   }
-  s = block_sum(s, sh);
+  const double s = block_sum(acc.value(), sh);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
 // d = z + beta d
 template <typename RV>
 __global__ void k_pcg_p(RV* __restrict__ d, const RV* __restrict__ z, const double* __restrict__ dscal, long long n) {
-  const double beta = dscal[S_BETA];
+  const RV beta = (RV)dscal[S_BETA];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    d[i] = (RV)((double)z[i] + beta * (double)d[i]);
+    d[i] = z[i] + beta * d[i];
 }
 
 // r = b - s (double); partials of r.r
@@ -258,6 +279,19 @@ __global__ void __launch_bounds__(1024) k_admm_finish(const double* __restrict__
   }
 }
 
+// Folded sub-problem residual, first half: with t = B y,
+//   v = q - M2^-1 t,  w = c - M1 y,
+// so that rhs - S y = (c + B^T q) - (M1 y + B^T M2^-1 B y) = w + B^T v.
+__global__ void k_fold(const double* __restrict__ t, const double* __restrict__ q, const double* __restrict__ c,
+                       const double* __restrict__ y, double m2inv0, double m2inv1, double m10, double m11,
+                       long long last_start, long long n, double* __restrict__ v, double* __restrict__ w) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const bool last = i >= last_start;
+    v[i] = q[i] - (last ? m2inv1 : m2inv0) * t[i];
+    w[i] = c[i] - (last ? m11 : m10) * y[i];
+  }
+}
+
 // dJ/dybar = -w (y - ybar); rhs of the adjoint: f = -w (y - ybar) - w_y
 __global__ void k_grad_ybar(const double* __restrict__ y, const double* __restrict__ ybar, const double* __restrict__ wy,
                             double w0, double w1, long long last_start, long long n, double* __restrict__ dJ,
@@ -364,6 +398,13 @@ cudaError_t admm_post(fde_problem* P, const AdmmArgs& A, const double* y, const 
   k_admm_post<<<g, kRedThreads, 0, st>>>(A, y, By, bu, r0, u, P->partials, g);
   note_launches(1);
   k_admm_finish<<<1, 1024, 0, st>>>(P->partials, g, P->dscal);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t fold(const double* t, const double* q, const double* c, const double* y, const double m2inv[2],
+                 const double m1[2], long long last_start, long long n, double* v, double* w, cudaStream_t st) {
+  k_fold<<<sgrid(n), 256, 0, st>>>(t, q, c, y, m2inv[0], m2inv[1], m1[0], m1[1], last_start, n, v, w);
   note_launches(1);
   return cudaGetLastError();
 }

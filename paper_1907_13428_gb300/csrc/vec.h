@@ -39,6 +39,8 @@ template <typename R> cudaError_t copy(R* dst, const R* src, long long n, cudaSt
 cudaError_t admm_pre(const AdmmArgs& A, double* c, double* bu, double* r0, double* q, cudaStream_t st);
 cudaError_t admm_post(fde_problem* P, const AdmmArgs& A, const double* y, const double* By, const double* bu,
                       const double* r0, double* u, cudaStream_t st);
+cudaError_t fold(const double* t, const double* q, const double* c, const double* y, const double m2inv[2],
+                 const double m1[2], long long last_start, long long n, double* v, double* w, cudaStream_t st);
 cudaError_t grad_ybar(const double* y, const double* ybar, const double* wy, double w0, double w1, long long last_start,
                       long long n, double* dJ, double* f, cudaStream_t st);
 cudaError_t precond_set_smem_attrs();
