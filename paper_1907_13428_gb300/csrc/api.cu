@@ -185,7 +185,8 @@ struct SolveInfo {
 // one double B^T, and leaves B y of the returned y in V_BY (by_valid = true).
 // The norm of rhs, used only for the relative stopping test, is formed in float.
 int subsolve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const double* rhs, const double* c,
-             const double* q, double* y, double tol, cudaStream_t st, SolveInfo* info, bool* by_valid) {
+             const double* q, double* y, double tol, cudaStream_t st, SolveInfo* info, bool by_on_entry,
+             bool* by_valid) {
   const long long N = P->N;
   *by_valid = false;
   if (o->precision == FDE_FP64) {
@@ -222,10 +223,14 @@ int subsolve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const doub
   auto A32 = [&](const float* x, float* out) { return op_S<float>(P, dg, x, out, s32, st); };
   auto M32 = [&](const float* r, float* z) { return op_M<float>(P, dg, r, z, st); };
   for (int k = 0; k <= maxref; ++k) {
-    CK(apply_B<double>(P, 0, y, P->v64[V_BY], nullptr, nullptr, nullptr, s64.t1, s64.t2, st));
+    // on entry V_BY already holds B y for the warm start (kept by the ADMM loop)
+    if (k > 0 || !by_on_entry) {
+      CK(apply_B<double>(P, 0, y, P->v64[V_BY], nullptr, nullptr, nullptr, s64.t1, s64.t2, st));
+      info->fp64_matvecs += 1;
+    }
     CK(fold(P->v64[V_BY], q, c, y, dg.M2inv.v, dg.M1.v, last, N, P->v64[V_SD], P->v64[V_Z], st));
     CK(apply_B<double>(P, 1, P->v64[V_SD], P->v64[V_R], nullptr, P->v64[V_Z], &one, s64.t1, s64.t2, st));
-    info->fp64_matvecs += 2;
+    info->fp64_matvecs += 1;
     *by_valid = true;
     CK((dot<double, double>(P, P->v64[V_R], P->v64[V_R], N, S_RR, FIN_STORE, st)));
     flag = read_scalars(P, st);
@@ -436,7 +441,8 @@ int fde_admm_solve(fde_problem* P, const fde_admm_opts* o, const double* ybar, c
   A.p = P->v64[V_P];
   A.wy = P->v64[V_WY];
   A.wu = P->v64[V_WU];
-  for (int i : {V_Y, V_U, V_ZY, V_ZU, V_P, V_WY, V_WU}) CK(fill<double>(P->v64[i], 0.0, N, st));
+  // zero iterates; V_BY = B y = 0 holds the invariant "V_BY = B Y" kept across iterations
+  for (int i : {V_Y, V_U, V_ZY, V_ZU, V_P, V_WY, V_WU, V_BY}) CK(fill<double>(P->v64[i], 0.0, N, st));
 
   fde_admm_stats S{};
   SolveInfo info;
@@ -459,7 +465,7 @@ int fde_admm_solve(fde_problem* P, const fde_admm_opts* o, const double* ybar, c
       tol = 0.05 * std::fmax(mn, o->tol_admm);
     }
     bool by_valid = false;
-    const int s = subsolve(P, dg, o, P->v64[V_RHS], P->v64[V_C], P->v64[V_Q], Y, tol, st, &info, &by_valid);
+    const int s = subsolve(P, dg, o, P->v64[V_RHS], P->v64[V_C], P->v64[V_Q], Y, tol, st, &info, true, &by_valid);
     if (s != FDE_OK && s != FDE_ENOCONV) {
       status = s;
       break;
