@@ -199,6 +199,37 @@ int fde_admm_grad(fde_problem* prob, const double* y, const double* ybar, const 
  * must be serialised by the caller. The work is queued on `stream`. */
 int fde_matvec_noalloc(const fde_params* params, int op, const double* x, double* y, void* stream);
 
+/* A batch of independent problems of different sizes and parameters (one
+ * fde_setup per instance; every axis of every instance must factor into 2, 3,
+ * 5 and 7). Errors: as fde_setup for any instance, FDE_EUNSUPPORTED. */
+typedef struct fde_batch fde_batch;
+int fde_batch_setup(const fde_params* params, int count, fde_batch** out, void* stream);
+void fde_batch_destroy(fde_batch* batch);
+/* N of instance i (0 when out of range). */
+long long fde_batch_instance_size(const fde_batch* batch, int i);
+
+/* Solve every instance of the batch with MIXED ADMM (Algorithm 1, Section 6.1
+ * psi scaling) in one CUDA-graph launch. Unlike fde_admm_solve, nothing is read
+ * back during the solve: each instance runs exactly opts->max_admm ADMM
+ * iterations; each sub-problem gets opts->max_refine double residual
+ * evaluations/float corrections (the last evaluation has no correction) and
+ * each correction exactly opts->max_pcg float PCG iterations, with
+ * convergence decided on the device (converged PCG iterations and corrections
+ * do no work on the iterates). opts->inner_tol is the sub-problem relative
+ * residual target, opts->inner_tol_mixed the float PCG target; tol_admm,
+ * fixed_iters and inner_tol_mode are ignored. The solve of the whole batch is
+ * captured into one CUDA graph (one independent branch per instance, run
+ * concurrently) on the first call and replayed while the arguments stay the
+ * same. Inputs: ybar[i] (device, N_i doubles); scalar bounds ya/yb/ua/ub
+ * (HOST arrays of `count` doubles, NULL = unbounded). Outputs: y[i], u[i]
+ * (device, N_i doubles); stats (HOST array of `count`, may be NULL;
+ * max_sub_relres is the largest final relative residual over the
+ * sub-problems). Synchronises `stream`. Errors: FDE_EINVAL (opts->precision
+ * not FDE_MIXED, NULL pointers, NaN bounds), FDE_ENONFINITE, FDE_ECUDA. */
+int fde_batch_admm_solve(fde_batch* batch, const fde_admm_opts* opts, const double* const* ybar,
+                         const double* ya, const double* yb, const double* ua, const double* ub,
+                         double* const* y, double* const* u, fde_admm_stats* stats, void* stream);
+
 /* Static message for a status code. */
 const char* fde_strerror(int status);
 

@@ -63,6 +63,11 @@ _SIGS = {
     "fde_last_cuda_error": (ctypes.c_char_p, []),
     "fde_kernel_launches": (ctypes.c_longlong, []),
     "fde_matvec_noalloc": (ctypes.c_int, [ctypes.POINTER(fde_params), ctypes.c_int, _P, _P, _P]),
+    "fde_batch_setup": (ctypes.c_int, [ctypes.POINTER(fde_params), ctypes.c_int, ctypes.POINTER(_P), _P]),
+    "fde_batch_destroy": (None, [_P]),
+    "fde_batch_instance_size": (ctypes.c_longlong, [_P, ctypes.c_int]),
+    "fde_batch_admm_solve": (ctypes.c_int, [_P, ctypes.POINTER(fde_admm_opts), _P, _P, _P, _P, _P, _P, _P,
+                                            ctypes.POINTER(fde_admm_stats), _P]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -235,6 +240,58 @@ class Problem:
                                    _ptr(wy, torch.float64, N), tol, _ptr(dJ), coef, _ptr(pv), _stream()),
                "fde_admm_grad")
         return dJ, torch.tensor(list(coef), dtype=torch.float64), pv
+
+
+class Batch:
+    """Owner of an fde_batch: independent instances solved together in one
+    CUDA-graph launch (fde_batch_admm_solve)."""
+
+    def __init__(self, params_list):
+        self.params = list(params_list)
+        n = len(self.params)
+        arr = (fde_params * n)(*[params_struct(p) for p in self.params])
+        h = ctypes.c_void_p()
+        _check(lib().fde_batch_setup(arr, n, ctypes.byref(h), _stream()), "fde_batch_setup")
+        self._h = h
+        self.sizes = [int(lib().fde_batch_instance_size(h, i)) for i in range(n)]
+        self._out = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fde_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def admm_solve(self, opts: AdmmOptions, ybars, ya=None, yb=None, ua=None, ub=None, out=None):
+        """ybars: list of CUDA float64 tensors (N_i); bounds: None or lists of floats.
+        Returns (ys, us, stats list). Output tensors are reused between calls so that
+        the captured graph can be replayed."""
+        n = len(self.sizes)
+        if out is None:
+            if self._out is None:
+                self._out = ([torch.empty(N, dtype=torch.float64, device=ybars[0].device) for N in self.sizes],
+                             [torch.empty(N, dtype=torch.float64, device=ybars[0].device) for N in self.sizes])
+            out = self._out
+        ys, us = out
+        P = ctypes.c_void_p
+        yb_ptrs = (P * n)(*[_ptr(t, torch.float64, N).value for t, N in zip(ybars, self.sizes)])
+        y_ptrs = (P * n)(*[t.data_ptr() for t in ys])
+        u_ptrs = (P * n)(*[t.data_ptr() for t in us])
+
+        def arr(v):
+            return None if v is None else (ctypes.c_double * n)(*[float(a) for a in v])
+
+        st = (fde_admm_stats * n)()
+        o = opts.c()
+        s = lib().fde_batch_admm_solve(self._h, ctypes.byref(o), yb_ptrs, arr(ya), arr(yb), arr(ua), arr(ub), y_ptrs,
+                                       u_ptrs, st, _stream())
+        _check(s, "fde_batch_admm_solve")
+        return ys, us, [x.as_dict() for x in st]
 
 
 class FdeAdmmFn(torch.autograd.Function):

@@ -75,6 +75,42 @@ Diags make_diags(const fde_problem* P, double delta, double rho) {
   return d;
 }
 
+AdmmArgs make_admm_args(fde_problem* P, const fde_admm_opts* o, const Diags& dg, const double* ybar, const double* g,
+                        const double* ya, const double* yb, const double* ua, const double* ub, double ya_s,
+                        double yb_s, double ua_s, double ub_s) {
+  AdmmArgs A{};
+  A.n = P->N;
+  A.last_start = (long long)(P->nt - 1) * P->nx * P->ny;
+  A.rho = o->rho;
+  A.delta = o->delta;
+  A.inv_delta = 1.0 / o->delta;
+  A.rho_over_delta = o->rho / o->delta;
+  A.delta_over_rho = o->delta / o->rho;
+  A.psi = P->psi;
+  A.gamma = P->prm.gamma;
+  for (int s = 0; s < 2; ++s) {
+    A.w[s] = dg.w.v[s];
+    A.Q[s] = dg.Q.v[s];
+    A.M2[s] = dg.M2.v[s];
+  }
+  A.ybar = ybar;
+  A.g = g;
+  A.ya = ya;
+  A.yb = yb;
+  A.ua = ua;
+  A.ub = ub;
+  A.ya_s = ya_s;
+  A.yb_s = yb_s;
+  A.ua_s = ua_s;
+  A.ub_s = ub_s;
+  A.zy = P->v64[V_ZY];
+  A.zu = P->v64[V_ZU];
+  A.p = P->v64[V_P];
+  A.wy = P->v64[V_WY];
+  A.wu = P->v64[V_WU];
+  return A;
+}
+
 bool valid_opts(const fde_admm_opts* o) {
   if (!o) return false;
   const double golden = (1.0 + std::sqrt(5.0)) / 2.0;
@@ -409,38 +445,9 @@ int fde_admm_solve(fde_problem* P, const fde_admm_opts* o, const double* ybar, c
   const long long N = P->N;
   const Diags dg = make_diags(P, o->delta, o->rho);
 
-  AdmmArgs A{};
-  A.n = N;
-  A.last_start = (long long)(P->nt - 1) * P->nx * P->ny;
-  A.rho = o->rho;
-  A.delta = o->delta;
-  A.inv_delta = 1.0 / o->delta;
-  A.rho_over_delta = o->rho / o->delta;
-  A.delta_over_rho = o->delta / o->rho;
-  A.psi = P->psi;
-  A.gamma = P->prm.gamma;
-  for (int s = 0; s < 2; ++s) {
-    A.w[s] = dg.w.v[s];
-    A.Q[s] = dg.Q.v[s];
-    A.M2[s] = dg.M2.v[s];
-  }
-  A.ybar = ybar;
-  A.g = g;
-  A.ya = ya;
-  A.yb = yb;
-  A.ua = ua;
-  A.ub = ub;
-  A.ya_s = ya_s;
-  A.yb_s = yb_s;
-  A.ua_s = ua_s;
-  A.ub_s = ub_s;
+  AdmmArgs A = make_admm_args(P, o, dg, ybar, g, ya, yb, ua, ub, ya_s, yb_s, ua_s, ub_s);
   double* Y = P->v64[V_Y];
   double* U = P->v64[V_U];
-  A.zy = P->v64[V_ZY];
-  A.zu = P->v64[V_ZU];
-  A.p = P->v64[V_P];
-  A.wy = P->v64[V_WY];
-  A.wu = P->v64[V_WU];
   // zero iterates; V_BY = B y = 0 holds the invariant "V_BY = B Y" kept across iterations
   for (int i : {V_Y, V_U, V_ZY, V_ZU, V_P, V_WY, V_WU, V_BY}) CK(fill<double>(P->v64[i], 0.0, N, st));
 
@@ -556,6 +563,258 @@ int fde_admm_grad(fde_problem* P, const double* y, const double* ybar, const dou
   if (p_out) CK(cudaMemcpyAsync(p_out, pv, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
   CK(cudaStreamSynchronize(st));
   return FDE_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Host-sync-free solve and batches of uneven instances.
+//
+// enqueue_admm_fixed queues a whole mixed-precision ADMM solve of one problem
+// on one stream without reading anything back: a fixed number of ADMM
+// iterations, of residual evaluations per sub-problem (max_refine + 1) and of
+// float PCG iterations per correction (max_pcg). Convergence is decided on
+// the device: a PCG iteration whose residual already met its threshold does
+// nothing (alpha = beta = 0), and a correction whose double residual already
+// met the sub-problem tolerance is skipped. Because nothing waits on the host,
+// the queued work can be captured into a CUDA graph; a batch captures one such
+// solve per instance on its own stream, forked from and joined to one capture
+// stream, so the graph has one independent branch per instance and a single
+// cudaGraphLaunch runs the whole batch.
+// ===========================================================================
+namespace {
+
+template <typename R, class OpA, class OpM>
+int pcg_fixed(fde_problem* P, OpA A, OpM M, const R* b, R* x, double tol, int iters, R* r, R* z, R* d, R* q,
+              cudaStream_t st) {
+  const long long N = P->N;
+  CK(fill<R>(x, (R)0, N, st));
+  CK(copy<R>(r, b, N, st));
+  CK((dot<R, R>(P, b, b, N, 0, FIN_BB_THR, st, tol)));
+  CK((dot<R, R>(P, r, r, N, S_RR, FIN_STORE, st)));
+  RK(M(r, z));
+  CK((dot<R, R>(P, r, z, N, 0, FIN_RZ0, st)));
+  CK(copy<R>(d, z, N, st));
+  for (int it = 0; it < iters; ++it) {
+    RK(A(d, q));
+    CK((dot<R, R>(P, d, q, N, 0, FIN_ALPHA_MASK, st)));
+    CK(pcg_xr<R>(P, x, r, d, q, N, st));
+    RK(M(r, z));
+    CK((dot<R, R>(P, r, z, N, 0, FIN_BETA_MASK, st)));
+    CK(pcg_p<R>(P, d, z, N, st));
+  }
+  return FDE_OK;
+}
+
+// Queue one mixed ADMM solve with scalar bounds; outputs y, u (device, N).
+int enqueue_admm_fixed(fde_problem* P, const fde_admm_opts* o, const double* ybar, double ya_s, double yb_s,
+                       double ua_s, double ub_s, double* y, double* u, cudaStream_t st) {
+  const long long N = P->N;
+  const Diags dg = make_diags(P, o->delta, o->rho);
+  AdmmArgs A = make_admm_args(P, o, dg, ybar, nullptr, nullptr, nullptr, nullptr, nullptr, ya_s, yb_s, ua_s, ub_s);
+  double* Y = P->v64[V_Y];
+  double* U = P->v64[V_U];
+  CK(cudaMemsetAsync(P->dscal, 0, sizeof(double) * S_COUNT, st));
+  for (int i : {V_Y, V_U, V_ZY, V_ZU, V_P, V_WY, V_WU, V_BY}) CK(fill<double>(P->v64[i], 0.0, N, st));
+  const long long last = (long long)(P->nt - 1) * P->nx * P->ny;
+  const SliceDiag one{{1.0, 1.0}};
+  auto s32 = scratch32(P);
+  auto s64 = scratch64(P);
+  auto A32 = [&](const float* xx, float* out) { return op_S<float>(P, dg, xx, out, s32, st); };
+  auto M32 = [&](const float* rr, float* zz) { return op_M<float>(P, dg, rr, zz, st); };
+  const double tol = o->inner_tol > 0 ? o->inner_tol : 1e-8;
+  const double inner = o->inner_tol_mixed > 0 ? o->inner_tol_mixed : 1e-4;
+  const int evals = (o->max_refine > 0 ? o->max_refine : 2) + 1;
+  for (int j = 0; j < o->max_admm; ++j) {
+    CK(admm_pre(A, P->v64[V_C], P->v64[V_BU], P->v64[V_R0], P->v64[V_Q], st));
+    // ||rhs||^2 of rhs = c + B^T q, in float (only the stopping test uses it)
+    CK(to_f32(P->v64[V_Q], P->v32[F_B], N, st));
+    CK(to_f32(P->v64[V_C], P->v32[F_R], N, st));
+    CK(apply_B<float>(P, 1, P->v32[F_B], P->v32[F_Z], nullptr, P->v32[F_R], &one, s32.t1, s32.t2, st));
+    CK((dot<float, float>(P, P->v32[F_Z], P->v32[F_Z], N, S_TMP0, FIN_STORE, st)));
+    for (int k = 0; k < evals; ++k) {
+      if (k > 0) CK(apply_B<double>(P, 0, Y, P->v64[V_BY], nullptr, nullptr, nullptr, s64.t1, s64.t2, st));
+      CK(fold(P->v64[V_BY], P->v64[V_Q], P->v64[V_C], Y, dg.M2inv.v, dg.M1.v, last, N, P->v64[V_SD], P->v64[V_Z],
+              st));
+      CK(apply_B<double>(P, 1, P->v64[V_SD], P->v64[V_R], nullptr, P->v64[V_Z], &one, s64.t1, s64.t2, st));
+      CK((dot<double, double>(P, P->v64[V_R], P->v64[V_R], N, 0, FIN_REFCHK, st, tol)));
+      if (k == evals - 1) break;
+      CK(to_f32_unless_conv(P, P->v64[V_R], P->v32[F_B], N, st));
+      RK(pcg_fixed<float>(P, A32, M32, P->v32[F_B], P->v32[F_X], inner, o->max_pcg, P->v32[F_R], P->v32[F_Z],
+                          P->v32[F_D], P->v32[F_Q], st));
+      CK(add_f32_unless_conv(P, Y, P->v32[F_X], N, st));
+    }
+    CK(scalar_max(P, S_MAXREL, S_RELRES, st));
+    CK(admm_post(P, A, Y, P->v64[V_BY], P->v64[V_BU], P->v64[V_R0], U, st));
+  }
+  CK(cudaMemcpyAsync(y, Y, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(u, U, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  return FDE_OK;
+}
+
+void stats_from_scalars(const double* h, int admm_iters, fde_admm_stats* S) {
+  *S = fde_admm_stats{};
+  S->admm_iters = admm_iters;
+  S->pcg_iters = (int)h[S_PCGIT];
+  S->refine_steps = (int)h[S_REFINE];
+  S->res_eq = h[S_RES_EQ];
+  S->res_y = h[S_RES_Y];
+  S->res_u = h[S_RES_U];
+  S->objective = h[S_OBJ];
+  S->max_sub_relres = h[S_MAXREL];
+}
+
+}  // namespace
+
+struct fde_batch {
+  int count = 0;
+  fde_problem** probs = nullptr;
+  cudaStream_t* streams = nullptr;
+  cudaEvent_t* joins = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t capture = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  // arguments the current graph was captured with
+  fde_admm_opts opts{};
+  const double** ybar = nullptr;
+  double** y = nullptr;
+  double** u = nullptr;
+  double* bounds = nullptr;  // 4 per instance: ya, yb, ua, ub
+};
+
+extern "C" {
+
+void fde_batch_destroy(fde_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (int i = 0; i < b->count; ++i) {
+    if (b->probs && b->probs[i]) fde_destroy(b->probs[i]);
+    if (b->streams && b->streams[i]) cudaStreamDestroy(b->streams[i]);
+    if (b->joins && b->joins[i]) cudaEventDestroy(b->joins[i]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  delete[] b->probs;
+  delete[] b->streams;
+  delete[] b->joins;
+  delete[] b->ybar;
+  delete[] b->y;
+  delete[] b->u;
+  delete[] b->bounds;
+  delete b;
+}
+
+int fde_batch_setup(const fde_params* params, int count, fde_batch** out, void* stream) {
+  if (!params || !out || count < 1) return FDE_EINVAL;
+  *out = nullptr;
+  fde_batch* b = new fde_batch();
+  b->count = count;
+  b->probs = new fde_problem*[count]();
+  b->streams = new cudaStream_t[count]();
+  b->joins = new cudaEvent_t[count]();
+  b->ybar = new const double*[count]();
+  b->y = new double*[count]();
+  b->u = new double*[count]();
+  b->bounds = new double[4 * count]();
+  for (int i = 0; i < count; ++i) {
+    const int s = fde_setup(&params[i], &b->probs[i], stream);
+    if (s != FDE_OK) {
+      fde_batch_destroy(b);
+      return s;
+    }
+    for (int a = 0; a < 3; ++a)
+      if (!b->probs[i]->ax[a].n_ok) {
+        fde_batch_destroy(b);
+        return FDE_EUNSUPPORTED;
+      }
+    cudaError_t e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      fde_batch_destroy(b);
+      return cuda_status(e);
+    }
+  }
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    fde_batch_destroy(b);
+    return cuda_status(e);
+  }
+  *out = b;
+  return FDE_OK;
+}
+
+long long fde_batch_instance_size(const fde_batch* b, int i) {
+  return (b && i >= 0 && i < b->count) ? b->probs[i]->N : 0;
+}
+
+int fde_batch_admm_solve(fde_batch* b, const fde_admm_opts* o, const double* const* ybar, const double* ya,
+                         const double* yb, const double* ua, const double* ub, double* const* y, double* const* u,
+                         fde_admm_stats* stats, void* stream) {
+  if (!b || !valid_opts(o) || !ybar || !y || !u) return FDE_EINVAL;
+  if (o->precision != FDE_MIXED || o->max_admm < 1 || o->max_pcg < 1) return FDE_EINVAL;
+  const int n = b->count;
+  bool same = b->exec && std::memcmp(&b->opts, o, sizeof(*o)) == 0;
+  for (int i = 0; i < n; ++i) {
+    if (!ybar[i] || !y[i] || !u[i]) return FDE_EINVAL;
+    const double bd[4] = {ya ? ya[i] : -INFINITY, yb ? yb[i] : INFINITY, ua ? ua[i] : -INFINITY,
+                          ub ? ub[i] : INFINITY};
+    for (int k = 0; k < 4; ++k) {
+      if (std::isnan(bd[k])) return FDE_EINVAL;
+      same = same && b->bounds[4 * i + k] == bd[k];
+    }
+    same = same && b->ybar[i] == ybar[i] && b->y[i] == y[i] && b->u[i] == u[i];
+  }
+  if (!same) {
+    // capture the batch: fork from the capture stream, one branch per instance, join
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
+    int status = FDE_OK;
+    cudaError_t e = cudaEventRecord(b->fork, b->capture);
+    for (int i = 0; i < n && status == FDE_OK && e == cudaSuccess; ++i) {
+      e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+      if (e != cudaSuccess) break;
+      const double bd[4] = {ya ? ya[i] : -INFINITY, yb ? yb[i] : INFINITY, ua ? ua[i] : -INFINITY,
+                            ub ? ub[i] : INFINITY};
+      status = enqueue_admm_fixed(b->probs[i], o, ybar[i], bd[0], bd[1], bd[2], bd[3], y[i], u[i], b->streams[i]);
+      if (status != FDE_OK) break;
+      e = cudaEventRecord(b->joins[i], b->streams[i]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->capture, b->joins[i], 0);
+      for (int k = 0; k < 4; ++k) b->bounds[4 * i + k] = bd[k];
+      b->ybar[i] = ybar[i];
+      b->y[i] = y[i];
+      b->u[i] = u[i];
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(b->capture, &graph);
+    if (status != FDE_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return status;
+    }
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_status(e != cudaSuccess ? e : e2);
+    }
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_status(e);
+    b->opts = *o;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaGraphLaunch(b->exec, st));
+  CK(cudaStreamSynchronize(st));
+  int status = FDE_OK;
+  for (int i = 0; i < n; ++i) {
+    fde_problem* P = b->probs[i];
+    CK(cudaMemcpy(P->hscal, P->dscal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost));
+    if (stats) stats_from_scalars(P->hscal, o->max_admm, &stats[i]);
+    const int flag = (int)P->hscal[S_FLAG];
+    if (flag < 0 && status == FDE_OK) status = flag;
+  }
+  return status;
 }
 
 }  // extern "C"

@@ -72,7 +72,15 @@ void note_launches(int n);
 // Device-scalar slots in fde_problem::dscal.
 enum Scal {
   S_RZ = 0, S_RZ_NEW, S_PQ, S_ALPHA, S_BETA, S_RR, S_BB, S_TMP0, S_TMP1, S_TMP2,
-  S_RES_EQ, S_RES_Y, S_RES_U, S_OBJ, S_FLAG, S_COUNT = 32
+  S_RES_EQ, S_RES_Y, S_RES_U, S_OBJ, S_FLAG,
+  // device-side control of the host-sync-free (graph) solve
+  S_THR,       // PCG stop threshold tol^2 ||b||^2
+  S_CONV,      // 1 when the current sub-problem's double residual met its tolerance
+  S_RELRES,    // last double relative residual of the sub-problem
+  S_MAXREL,    // largest final relative residual over the sub-problems
+  S_PCGIT,     // PCG iterations that did work (counted on the device)
+  S_REFINE,    // refinement corrections that did work
+  S_COUNT = 32
 };
 
 // ---- launchers (each returns cudaError_t of the launch) ----

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dot(const RA* __restrict__ a, c
 //   op FIN_ALPHA: dscal[S_PQ] = sum; alpha = rz / sum (flag breakdown if sum <= 0)
 //   op FIN_BETA : beta = sum / rz; rz = sum
 __global__ void __launch_bounds__(1024) k_finish(const double* __restrict__ partials, int np, double* dscal, int slot,
-                                                  int op) {
+                                                  int op, double aux) {
   __shared__ double sh[32];
   double s = 0.0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) s += partials[i];
@@ -105,6 +105,25 @@ __global__ void __launch_bounds__(1024) k_finish(const double* __restrict__ part
       dscal[S_RZ] = s;
     } else if (op == FIN_RZ0) {
       dscal[S_RZ] = s;
+    } else if (op == FIN_BB_THR) {
+      dscal[S_BB] = s;
+      dscal[S_THR] = aux * aux * s;
+    } else if (op == FIN_ALPHA_MASK) {
+      dscal[S_PQ] = s;
+      const bool active = dscal[S_RR] > dscal[S_THR] && s > 0.0 && isfinite(s);
+      dscal[S_ALPHA] = active ? dscal[S_RZ] / s : 0.0;
+      if (active) dscal[S_PCGIT] += 1.0;
+    } else if (op == FIN_BETA_MASK) {
+      const double rz = dscal[S_RZ];
+      const bool active = dscal[S_RR] > dscal[S_THR] && rz != 0.0;
+      dscal[S_BETA] = active ? s / rz : 0.0;
+      dscal[S_RZ] = s;
+    } else if (op == FIN_REFCHK) {
+      dscal[S_RR] = s;
+      const double bb = dscal[S_TMP0];
+      const double rel = bb > 0.0 ? sqrt(s / bb) : 0.0;
+      dscal[S_RELRES] = rel;
+      dscal[S_CONV] = (rel <= aux) ? 1.0 : 0.0;
     }
   }
 }
@@ -154,6 +173,28 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(const double* __restri
 __global__ void k_to_f32(const double* __restrict__ in, float* __restrict__ out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = (float)in[i];
+}
+
+// out32 = conv ? 0 : (float) in64 (conv read from the device)
+__global__ void k_to_f32_unless(const double* __restrict__ in, float* __restrict__ out, long long n,
+                                const double* __restrict__ dscal) {
+  const bool conv = dscal[S_CONV] != 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = conv ? 0.f : (float)in[i];
+}
+
+// y64 += (double) d32 unless conv; block 0 counts the applied correction
+__global__ void k_add_f32_unless(double* __restrict__ y, const float* __restrict__ d, long long n,
+                                 double* __restrict__ dscal) {
+  const bool conv = dscal[S_CONV] != 0.0;
+  if (conv) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += (double)d[i];
+}
+
+__global__ void k_scalar_step(double* dscal, int dst, int src, int op) {
+  if (op == 0) dscal[dst] = fmax(dscal[dst], dscal[src]);
+  else if (op == 1 && dscal[S_CONV] == 0.0) dscal[S_REFINE] += 1.0;
 }
 
 // y64 += (double) d32
@@ -315,23 +356,26 @@ static unsigned sgrid(long long n) {
 }
 
 template <typename RA, typename RB>
-cudaError_t dot(fde_problem* P, const RA* a, const RB* b, long long n, int slot, int op, cudaStream_t st) {
+cudaError_t dot(fde_problem* P, const RA* a, const RB* b, long long n, int slot, int op, cudaStream_t st,
+                double aux) {
   const int g = red_grid(n);
   k_dot<RA, RB><<<g, kRedThreads, 0, st>>>(a, b, n, P->partials);
   note_launches(1);
-  k_finish<<<1, 1024, 0, st>>>(P->partials, g, P->dscal, slot, op);
+  k_finish<<<1, 1024, 0, st>>>(P->partials, g, P->dscal, slot, op, aux);
   note_launches(1);
   return cudaGetLastError();
 }
-template cudaError_t dot<double, double>(fde_problem*, const double*, const double*, long long, int, int, cudaStream_t);
-template cudaError_t dot<float, float>(fde_problem*, const float*, const float*, long long, int, int, cudaStream_t);
+template cudaError_t dot<double, double>(fde_problem*, const double*, const double*, long long, int, int, cudaStream_t,
+                                         double);
+template cudaError_t dot<float, float>(fde_problem*, const float*, const float*, long long, int, int, cudaStream_t,
+                                       double);
 
 template <typename RV>
 cudaError_t pcg_xr(fde_problem* P, RV* x, RV* r, const RV* d, const RV* q, long long n, cudaStream_t st) {
   const int g = red_grid(n);
   k_pcg_xr<RV><<<g, kRedThreads, 0, st>>>(x, r, d, q, P->dscal, n, P->partials);
   note_launches(1);
-  k_finish<<<1, 1024, 0, st>>>(P->partials, g, P->dscal, S_RR, FIN_STORE);
+  k_finish<<<1, 1024, 0, st>>>(P->partials, g, P->dscal, S_RR, FIN_STORE, 0.0);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -353,13 +397,30 @@ cudaError_t residual(fde_problem* P, const double* b, const double* s, double* r
   const int g = red_grid(n);
   k_residual<<<g, kRedThreads, 0, st>>>(b, s, r, n, P->partials);
   note_launches(1);
-  k_finish<<<1, 1024, 0, st>>>(P->partials, g, P->dscal, slot, FIN_STORE);
+  k_finish<<<1, 1024, 0, st>>>(P->partials, g, P->dscal, slot, FIN_STORE, 0.0);
   note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t to_f32(const double* in, float* out, long long n, cudaStream_t st) {
   k_to_f32<<<sgrid(n), 256, 0, st>>>(in, out, n);
+  note_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t to_f32_unless_conv(fde_problem* P, const double* in, float* out, long long n, cudaStream_t st) {
+  k_to_f32_unless<<<sgrid(n), 256, 0, st>>>(in, out, n, P->dscal);
+  note_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t add_f32_unless_conv(fde_problem* P, double* y, const float* d, long long n, cudaStream_t st) {
+  k_scalar_step<<<1, 1, 0, st>>>(P->dscal, 0, 0, 1);
+  note_launches(1);
+  k_add_f32_unless<<<sgrid(n), 256, 0, st>>>(y, d, n, P->dscal);
+  note_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t scalar_max(fde_problem* P, int dst, int src, cudaStream_t st) {
+  k_scalar_step<<<1, 1, 0, st>>>(P->dscal, dst, src, 0);
   note_launches(1);
   return cudaGetLastError();
 }
