@@ -199,13 +199,13 @@ int pcg(fde_problem* P, OpA A, OpM M, const R* b, R* x, bool x_zero, double tol,
 }
 
 template <typename R>
-int op_S(fde_problem* P, const Diags& dg, const R* x, R* y, Scratch<R> s, cudaStream_t st) {
-  CK(apply_S<R>(P, dg.M1, dg.M2inv, x, y, s.w, s.t1, s.t2, st));
+int op_S(fde_problem* P, const Diags& dg, const R* x, R* y, Scratch<R> s, cudaStream_t st, Gate gate = {}) {
+  CK(apply_S<R>(P, dg.M1, dg.M2inv, x, y, s.w, s.t1, s.t2, st, gate));
   return FDE_OK;
 }
 template <typename R>
-int op_M(fde_problem* P, const Diags& dg, const R* r, R* z, cudaStream_t st) {
-  CK(apply_precond<R>(P, dg.m1, dg.m2, 0, r, z, spec<R>(P), st));
+int op_M(fde_problem* P, const Diags& dg, const R* r, R* z, cudaStream_t st, Gate gate = {}) {
+  CK(apply_precond<R>(P, dg.m1, dg.m2, 0, r, z, spec<R>(P), st, gate));
   return FDE_OK;
 }
 
@@ -620,8 +620,11 @@ int enqueue_admm_fixed(fde_problem* P, const fde_admm_opts* o, const double* yba
   const SliceDiag one{{1.0, 1.0}};
   auto s32 = scratch32(P);
   auto s64 = scratch64(P);
-  auto A32 = [&](const float* xx, float* out) { return op_S<float>(P, dg, xx, out, s32, st); };
-  auto M32 = [&](const float* rr, float* zz) { return op_M<float>(P, dg, rr, zz, st); };
+  // float PCG transforms do no work once the PCG has converged; double products
+  // after the first residual evaluation do none once the refinement has
+  const Gate pcg_gate{P->dscal, 1}, ref_gate{P->dscal, 2};
+  auto A32 = [&](const float* xx, float* out) { return op_S<float>(P, dg, xx, out, s32, st, pcg_gate); };
+  auto M32 = [&](const float* rr, float* zz) { return op_M<float>(P, dg, rr, zz, st, pcg_gate); };
   const double tol = o->inner_tol > 0 ? o->inner_tol : 1e-8;
   const double inner = o->inner_tol_mixed > 0 ? o->inner_tol_mixed : 1e-4;
   const int evals = (o->max_refine > 0 ? o->max_refine : 2) + 1;
@@ -633,10 +636,12 @@ int enqueue_admm_fixed(fde_problem* P, const fde_admm_opts* o, const double* yba
     CK(apply_B<float>(P, 1, P->v32[F_B], P->v32[F_Z], nullptr, P->v32[F_R], &one, s32.t1, s32.t2, st));
     CK((dot<float, float>(P, P->v32[F_Z], P->v32[F_Z], N, S_TMP0, FIN_STORE, st)));
     for (int k = 0; k < evals; ++k) {
-      if (k > 0) CK(apply_B<double>(P, 0, Y, P->v64[V_BY], nullptr, nullptr, nullptr, s64.t1, s64.t2, st));
+      // once converged, y and hence B y and the residual are unchanged: skip the products
+      const Gate g = k > 0 ? ref_gate : Gate{};
+      if (k > 0) CK(apply_B<double>(P, 0, Y, P->v64[V_BY], nullptr, nullptr, nullptr, s64.t1, s64.t2, st, g));
       CK(fold(P->v64[V_BY], P->v64[V_Q], P->v64[V_C], Y, dg.M2inv.v, dg.M1.v, last, N, P->v64[V_SD], P->v64[V_Z],
               st));
-      CK(apply_B<double>(P, 1, P->v64[V_SD], P->v64[V_R], nullptr, P->v64[V_Z], &one, s64.t1, s64.t2, st));
+      CK(apply_B<double>(P, 1, P->v64[V_SD], P->v64[V_R], nullptr, P->v64[V_Z], &one, s64.t1, s64.t2, st, g));
       CK((dot<double, double>(P, P->v64[V_R], P->v64[V_R], N, 0, FIN_REFCHK, st, tol)));
       if (k == evals - 1) break;
       CK(to_f32_unless_conv(P, P->v64[V_R], P->v32[F_B], N, st));

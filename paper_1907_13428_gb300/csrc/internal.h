@@ -36,6 +36,15 @@ struct Axis {
   AxisTables<float> f;
 };
 
+// Device-side gate of a transform launch in the host-sync-free solve: the
+// kernel returns at once when its instance's PCG has converged (mode 1:
+// dscal[S_RR] <= dscal[S_THR]) or its refinement has (mode 2: dscal[S_CONV]).
+// mode 0: always run. The slot indices are those of fde::Scal.
+struct Gate {
+  const double* dscal = nullptr;
+  int mode = 0;
+};
+
 // Per-time-slice diagonal: value on slices 0..nt-2 and on the last slice.
 struct SliceDiag {
   double v[2];
@@ -83,6 +92,12 @@ enum Scal {
   S_COUNT = 32
 };
 
+__device__ __forceinline__ bool gate_closed(const Gate& g) {
+  if (g.mode == 1) return g.dscal[S_RR] <= g.dscal[S_THR];
+  if (g.mode == 2) return g.dscal[S_CONV] != 0.0;
+  return false;
+}
+
 // ---- launchers (each returns cudaError_t of the launch) ----
 
 // Set-up of the axis tables (setup.cu).
@@ -93,11 +108,11 @@ cudaError_t setup_axis_tables(fde_problem* P, cudaStream_t st);
 //   (M2^-1 for S). If addv != null, addc(t) * addv is added after that.
 template <typename R>
 cudaError_t apply_B(fde_problem* P, int transpose, const R* x, R* y, const SliceDiag* dscale,
-                    const R* addv, const SliceDiag* addc, R* tmp1, R* tmp2, cudaStream_t st);
+                    const R* addv, const SliceDiag* addc, R* tmp1, R* tmp2, cudaStream_t st, Gate gate = {});
 // y = S x = M1 x + B^T (M2^-1 B x), using w (N) and tmp1, tmp2 (N) as scratch.
 template <typename R>
 cudaError_t apply_S(fde_problem* P, const SliceDiag& M1, const SliceDiag& M2inv, const R* x, R* y,
-                    R* w, R* tmp1, R* tmp2, cudaStream_t st);
+                    R* w, R* tmp1, R* tmp2, cudaStream_t st, Gate gate = {});
 // One spatial factor along one axis (1: x1, 2: x2) with the given symbol
 // halves (e.g. AxisTables::symL for the one-sided L), no time term, for the gradient.
 template <typename R>
@@ -108,7 +123,7 @@ cudaError_t apply_axis_raw(fde_problem* P, int axis, const R* x, R* y, const cpl
 // (m1, m2); mode 1: (C3 C3^T)^-1 (the adjoint normal-equation preconditioner).
 template <typename R>
 cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const R* r, R* z,
-                          cplx<R>* spec, cudaStream_t st);
+                          cplx<R>* spec, cudaStream_t st, Gate gate = {});
 
 
 }  // namespace fde

@@ -30,7 +30,8 @@ template <> const AxisTables<float>& ptables<float>(const Axis& A) { return A.f;
 template <typename R>
 __global__ void __launch_bounds__(512) k_prec_rows_fwd(const R* __restrict__ r, cplx<R>* __restrict__ spec,
                                                         long long nrows, int n, int H, int Hp,
-                                                        const cplx<R>* __restrict__ twn, FftPlan pl, int pairs) {
+                                                        const cplx<R>* __restrict__ twn, FftPlan pl, int pairs, Gate gate) {
+  if (gate_closed(gate)) return;
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -62,7 +63,8 @@ __global__ void __launch_bounds__(512) k_prec_rows_fwd(const R* __restrict__ r, 
 template <typename R>
 __global__ void __launch_bounds__(512) k_prec_rows_inv(const cplx<R>* __restrict__ spec, R* __restrict__ z,
                                                         long long nrows, int n, int H, int Hp,
-                                                        const cplx<R>* __restrict__ twn, FftPlan pl, int pairs) {
+                                                        const cplx<R>* __restrict__ twn, FftPlan pl, int pairs, Gate gate) {
+  if (gate_closed(gate)) return;
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -99,6 +101,7 @@ struct DivArgs {
   int adjoint;    // 1: sigma = |Lambda|^2
   double m1, inv_m2, psi, inv_N;
   int Hp, H;
+  Gate gate;  // device-side skip of the launch (host-sync-free solve)
 };
 
 template <typename R>
@@ -107,6 +110,7 @@ __global__ void __launch_bounds__(1024) k_prec_axis(cplx<R>* __restrict__ spec, 
                                                      const cplx<R>* __restrict__ twn, FftPlan pl, int inverse,
                                                      int lines, DivArgs dv, const cplx<R>* __restrict__ lt,
                                                      const cplx<R>* __restrict__ lx, const cplx<R>* __restrict__ ly) {
+  if (gate_closed(dv.gate)) return;
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -160,12 +164,12 @@ cudaError_t launch_prec_axis_reg(int L, cplx<R>* spec, long long axis_stride, lo
 cudaError_t precond_reg_set_smem_attrs();
 template <typename R>
 cudaError_t launch_prec_rows_reg(int L, int inverse, const R* r, R* z, cplx<R>* spec, long long nrows, int H, int Hp,
-                                 const cplx<R>* twn, cudaStream_t st);
+                                 const cplx<R>* twn, cudaStream_t st, Gate gate);
 cudaError_t precond_rows_reg_set_smem_attrs();
 
 template <typename R>
 cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const R* r, R* z, cplx<R>* spec,
-                          cudaStream_t st) {
+                          cudaStream_t st, Gate gate) {
   using C = cplx<R>;
   const Axis& At = P->ax[0];
   const Axis& Ax = P->ax[1];
@@ -176,7 +180,8 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
   const bool rows_pow2 = ny >= 16 && (ny & (ny - 1)) == 0;
   // 1. rows forward
   if (rows_pow2) {
-    if ((err = launch_prec_rows_reg<R>(ny, 0, r, nullptr, spec, nrows, H, Hp, ptables<R>(Ay).twn, st)) != cudaSuccess)
+    if ((err = launch_prec_rows_reg<R>(ny, 0, r, nullptr, spec, nrows, H, Hp, ptables<R>(Ay).twn, st, gate)) !=
+        cudaSuccess)
       return err;
   } else {
     const int threads = (ny > kPEPT * 256) ? 512 : 256;
@@ -186,13 +191,14 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
     if (pairs > np) pairs = (int)np;
     const long long grid = (np + pairs - 1) / pairs;
     k_prec_rows_fwd<R><<<(unsigned)grid, threads, (size_t)pairs * ny * sizeof(C), st>>>(
-        r, spec, nrows, ny, H, Hp, ptables<R>(Ay).twn, Ay.plann, pairs);
+        r, spec, nrows, ny, H, Hp, ptables<R>(Ay).twn, Ay.plann, pairs, gate);
   note_launches(1);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   const int threads = sizeof(R) == 4 ? 1024 : 512;
   const int cap = kPEPT * threads;
   DivArgs none{};
+  none.gate = gate;
   // 2. x1 forward; 3. t forward/divide/inverse; 4. x1 inverse
   for (int step = 0; step < 3; ++step) {
     const bool tpass = (step == 1);
@@ -242,7 +248,8 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
   }
   // 5. rows inverse
   if (rows_pow2) {
-    if ((err = launch_prec_rows_reg<R>(ny, 1, nullptr, z, spec, nrows, H, Hp, ptables<R>(Ay).twn, st)) != cudaSuccess)
+    if ((err = launch_prec_rows_reg<R>(ny, 1, nullptr, z, spec, nrows, H, Hp, ptables<R>(Ay).twn, st, gate)) !=
+        cudaSuccess)
       return err;
   } else {
     const int threads2 = (ny > kPEPT * 256) ? 512 : 256;
@@ -252,7 +259,7 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
     if (pairs > np) pairs = (int)np;
     const long long grid = (np + pairs - 1) / pairs;
     k_prec_rows_inv<R><<<(unsigned)grid, threads2, (size_t)pairs * ny * sizeof(C), st>>>(
-        spec, z, nrows, ny, H, Hp, ptables<R>(Ay).twn, Ay.plann, pairs);
+        spec, z, nrows, ny, H, Hp, ptables<R>(Ay).twn, Ay.plann, pairs, gate);
   note_launches(1);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
@@ -260,9 +267,9 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
 }
 
 template cudaError_t apply_precond<double>(fde_problem*, double, double, int, const double*, double*, double2*,
-                                           cudaStream_t);
+                                           cudaStream_t, Gate);
 template cudaError_t apply_precond<float>(fde_problem*, double, double, int, const float*, float*, float2*,
-                                          cudaStream_t);
+                                          cudaStream_t, Gate);
 
 // Dynamic shared memory above 48 KB must be opted into per kernel.
 cudaError_t precond_set_smem_attrs() {
@@ -305,6 +312,7 @@ __global__ void __launch_bounds__(NT) k_prec_axis_reg(cplx<R>* __restrict__ spec
                                                        const cplx<R>* __restrict__ twn, int mode, DivArgs dv,
                                                        const cplx<R>* __restrict__ lt, const cplx<R>* __restrict__ lx,
                                                        const cplx<R>* __restrict__ ly) {
+  if (gate_closed(dv.gate)) return;
   using C = cplx<R>;
   constexpr int T = L / 16, CP = NT / T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -436,7 +444,8 @@ namespace fde {
 template <typename R, int L, int NT>
 __global__ void __launch_bounds__(NT) k_prec_rows_fwd_reg(const R* __restrict__ r, cplx<R>* __restrict__ spec,
                                                            long long nrows, int H, int Hp,
-                                                           const cplx<R>* __restrict__ twn) {
+                                                           const cplx<R>* __restrict__ twn, Gate gate) {
+  if (gate_closed(gate)) return;
   using C = cplx<R>;
   constexpr int T = L / 16, PAIRS = NT / T, LS = L + L / 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -472,7 +481,8 @@ __global__ void __launch_bounds__(NT) k_prec_rows_fwd_reg(const R* __restrict__ 
 template <typename R, int L, int NT>
 __global__ void __launch_bounds__(NT) k_prec_rows_inv_reg(const cplx<R>* __restrict__ spec, R* __restrict__ z,
                                                            long long nrows, int H, int Hp,
-                                                           const cplx<R>* __restrict__ twn) {
+                                                           const cplx<R>* __restrict__ twn, Gate gate) {
+  if (gate_closed(gate)) return;
   using C = cplx<R>;
   constexpr int T = L / 16, PAIRS = NT / T, LS = L + L / 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -506,26 +516,26 @@ __global__ void __launch_bounds__(NT) k_prec_rows_inv_reg(const cplx<R>* __restr
 
 template <typename R, int L>
 static cudaError_t launch_prec_rows_reg_L(int inverse, const R* r, R* z, cplx<R>* spec, long long nrows, int H,
-                                          int Hp, const cplx<R>* twn, cudaStream_t st) {
+                                          int Hp, const cplx<R>* twn, cudaStream_t st, Gate gate) {
   constexpr int NT = 256;
   constexpr int PAIRS = NT / (L / 16);
   const long long npairs = (nrows + 1) / 2;
   const long long grid = (npairs + PAIRS - 1) / PAIRS;
   const size_t smem = (size_t)PAIRS * (L + L / 16) * sizeof(cplx<R>);
   if (inverse)
-    k_prec_rows_inv_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(spec, z, nrows, H, Hp, twn);
+    k_prec_rows_inv_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(spec, z, nrows, H, Hp, twn, gate);
   else
-    k_prec_rows_fwd_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(r, spec, nrows, H, Hp, twn);
+    k_prec_rows_fwd_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(r, spec, nrows, H, Hp, twn, gate);
   note_launches(1);
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_prec_rows_reg(int L, int inverse, const R* r, R* z, cplx<R>* spec, long long nrows, int H, int Hp,
-                                 const cplx<R>* twn, cudaStream_t st) {
+                                 const cplx<R>* twn, cudaStream_t st, Gate gate) {
   switch (L) {
 #define FDE_CASE(LL) \
-  case LL: return launch_prec_rows_reg_L<R, LL>(inverse, r, z, spec, nrows, H, Hp, twn, st);
+  case LL: return launch_prec_rows_reg_L<R, LL>(inverse, r, z, spec, nrows, H, Hp, twn, st, gate);
     FDE_FOR_EACH_PL(FDE_CASE)
 #undef FDE_CASE
     default: return cudaErrorInvalidValue;
@@ -533,9 +543,9 @@ cudaError_t launch_prec_rows_reg(int L, int inverse, const R* r, R* z, cplx<R>* 
 }
 
 template cudaError_t launch_prec_rows_reg<float>(int, int, const float*, float*, float2*, long long, int, int,
-                                                 const float2*, cudaStream_t);
+                                                 const float2*, cudaStream_t, Gate);
 template cudaError_t launch_prec_rows_reg<double>(int, int, const double*, double*, double2*, long long, int, int,
-                                                  const double2*, cudaStream_t);
+                                                  const double2*, cudaStream_t, Gate);
 
 cudaError_t precond_rows_reg_set_smem_attrs() {
   const int big = 200 * 1024;

@@ -44,6 +44,7 @@ template <typename R> struct AxisEpi {
   R dsc0, dsc1;
   const R* addv;  // nullable
   R addc0, addc1;
+  Gate gate;      // device-side skip of the whole launch (host-sync-free solve)
 };
 
 template <typename R>
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(512) k_rows(const R* __restrict__ x, long long
                                                const cplx<R>* __restrict__ sym, const cplx<R>* __restrict__ tw2,
                                                const cplx<R>* __restrict__ twL, FftPlan pl, int conj_sym, int pairs,
                                                AxisEpi<R> E) {
+  if (gate_closed(E.gate)) return;
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -163,6 +165,7 @@ __global__ void __launch_bounds__(1024) k_axis(const R* __restrict__ x, int n, i
                                                 const cplx<R>* __restrict__ sym, const cplx<R>* __restrict__ tw2,
                                                 const cplx<R>* __restrict__ twL, FftPlan pl, int conj_sym,
                                                 int pairs, AxisEpi<R> E) {
+  if (gate_closed(E.gate)) return;
   using C = cplx<R>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -282,7 +285,7 @@ static cudaError_t launch_axis(fde_problem* P, int axis, const R* x, int conj_sy
 
 template <typename R>
 cudaError_t apply_B(fde_problem* P, int transpose, const R* x, R* y, const SliceDiag* dscale, const R* addv,
-                    const SliceDiag* addc, R* tmp1, R* tmp2, cudaStream_t st) {
+                    const SliceDiag* addc, R* tmp1, R* tmp2, cudaStream_t st, Gate gate) {
   // x1 pass first (plain store), then the optional time pass, then the x2 pass,
   // whose coalesced epilogue adds the partial results, the implicit-Euler time
   // term, the per-slice diagonal and the addend.
@@ -290,6 +293,7 @@ cudaError_t apply_B(fde_problem* P, int transpose, const R* x, R* y, const Slice
   Ex.out = tmp1;
   Ex.nt = P->nt;
   Ex.plain = 1;
+  Ex.gate = gate;
   // implicit Euler: the x1 symbol shifted by psi/h_t also adds +psi/h_t x_t
   const cplx<R>* symD = P->euler ? tables<R>(P->ax[1]).symD : nullptr;
   cudaError_t err = launch_axis<R>(P, 1, x, transpose, symD, Ex, st);
@@ -301,6 +305,7 @@ cudaError_t apply_B(fde_problem* P, int transpose, const R* x, R* y, const Slice
     Et.acc = tmp1;
     Et.nt = P->nt;
     Et.t_is_axis = 1;
+    Et.gate = gate;
     err = launch_axis<R>(P, 0, x, transpose, nullptr, Et, st);
     if (err != cudaSuccess) return err;
     acc = tmp2;
@@ -311,6 +316,7 @@ cudaError_t apply_B(fde_problem* P, int transpose, const R* x, R* y, const Slice
   E.nt = P->nt;
   E.plane = (long long)P->nx * P->ny;
   E.rows_per_slice = P->nx;
+  E.gate = gate;
   if (P->euler) {
     E.xt = x;
     E.tdir = transpose ? -1 : 1;
@@ -332,10 +338,10 @@ cudaError_t apply_B(fde_problem* P, int transpose, const R* x, R* y, const Slice
 
 template <typename R>
 cudaError_t apply_S(fde_problem* P, const SliceDiag& M1, const SliceDiag& M2inv, const R* x, R* y, R* w, R* tmp1,
-                    R* tmp2, cudaStream_t st) {
-  cudaError_t err = apply_B<R>(P, 0, x, w, &M2inv, nullptr, nullptr, tmp1, tmp2, st);
+                    R* tmp2, cudaStream_t st, Gate gate) {
+  cudaError_t err = apply_B<R>(P, 0, x, w, &M2inv, nullptr, nullptr, tmp1, tmp2, st, gate);
   if (err != cudaSuccess) return err;
-  return apply_B<R>(P, 1, w, y, nullptr, x, &M1, tmp1, tmp2, st);
+  return apply_B<R>(P, 1, w, y, nullptr, x, &M1, tmp1, tmp2, st, gate);
 }
 
 template <typename R>
@@ -353,13 +359,13 @@ cudaError_t apply_axis_raw(fde_problem* P, int axis, const R* x, R* y, const cpl
 }
 
 template cudaError_t apply_B<double>(fde_problem*, int, const double*, double*, const SliceDiag*, const double*,
-                                     const SliceDiag*, double*, double*, cudaStream_t);
+                                     const SliceDiag*, double*, double*, cudaStream_t, Gate);
 template cudaError_t apply_B<float>(fde_problem*, int, const float*, float*, const SliceDiag*, const float*,
-                                    const SliceDiag*, float*, float*, cudaStream_t);
+                                    const SliceDiag*, float*, float*, cudaStream_t, Gate);
 template cudaError_t apply_S<double>(fde_problem*, const SliceDiag&, const SliceDiag&, const double*, double*,
-                                     double*, double*, double*, cudaStream_t);
+                                     double*, double*, double*, cudaStream_t, Gate);
 template cudaError_t apply_S<float>(fde_problem*, const SliceDiag&, const SliceDiag&, const float*, float*, float*,
-                                    float*, float*, cudaStream_t);
+                                    float*, float*, cudaStream_t, Gate);
 template cudaError_t apply_axis_raw<double>(fde_problem*, int, const double*, double*, const double2*, int,
                                             cudaStream_t);
 
@@ -393,6 +399,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const
                                                   int n, const cplx<R>* __restrict__ sym,
                                                   const cplx<R>* __restrict__ tw2, const cplx<R>* __restrict__ twL,
                                                   int conj_sym, AxisEpi<R> E) {
+  if (gate_closed(E.gate)) return;
   using C = cplx<R>;
   constexpr int T = L / 16, PAIRS = NT / T, LS = L + L / 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -461,6 +468,7 @@ __global__ void __launch_bounds__(NT) k_axis_reg(const R* __restrict__ x, int n,
                                                   const cplx<R>* __restrict__ sym, const cplx<R>* __restrict__ tw2,
                                                   const cplx<R>* __restrict__ twL, int conj_sym, AxisEpi<R> E,
                                                   int vec2) {
+  if (gate_closed(E.gate)) return;
   using C = cplx<R>;
   constexpr int T = L / 16, CP = NT / T, LW = 2 * CP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
