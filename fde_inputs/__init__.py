@@ -173,9 +173,10 @@ def config_grad_small() -> FdeInstance:
     return FdeInstance(p, desired_state_sine(p, MASTER_SEED), None, None, None, -1.0, 1.0, MASTER_SEED)
 
 
-def config_batch(count: int = 64, seed0: int = MASTER_SEED):
-    """Uneven batch: grids {64^2,128^2,256^2,512^2}, nt {16,32,64}, random orders,
-    log-uniform gamma in [1e-6, 1e-2], control bounds u_b~U(0.25,2), u_a=-U(0.25,2)."""
+def config_batch_params(count: int = 64, seed0: int = MASTER_SEED):
+    """Parameters and control bounds of the uneven batch: grids {64^2,128^2,256^2,512^2},
+    nt {16,32,64}, orders U(1.1,1.9), gamma log-uniform in [1e-6, 1e-2],
+    u_b ~ U(0.25, 2), u_a = -U(0.25, 2). Returns [(params, ua, ub, seed)]."""
     out = []
     for k in range(count):
         s = seed0 + k
@@ -189,5 +190,11 @@ def config_batch(count: int = 64, seed0: int = MASTER_SEED):
         ua = -(0.25 + 1.75 * u[6])
         p = FdeParams(nx=n, ny=n, nt=nt, T=1.0, beta_x=bx, beta_y=by, alpha_t=1.0,
                       dp=1.0, dm=0.5, ep=0.8, em=0.3, gamma=gamma)
-        out.append(FdeInstance(p, desired_state_sine(p, s), None, None, None, ua, ub, s))
+        out.append((p, ua, ub, s))
     return out
+
+
+def config_batch(count: int = 64, seed0: int = MASTER_SEED):
+    """The uneven batch with desired states (see config_batch_params)."""
+    return [FdeInstance(p, desired_state_sine(p, s), None, None, None, ua, ub, s)
+            for p, ua, ub, s in config_batch_params(count, seed0)]

@@ -510,14 +510,18 @@ def kkt_solve(inst, act_y_lo, act_y_hi, act_u_lo, act_u_hi, B=None) -> KktSoluti
     uA = np.where(act_u_lo.ravel(), lo_u, np.where(act_u_hi.ravel(), hi_u, 0.0))
     if B is None:
         B = assemble_B_sparse(p)
-    Bd = B.toarray() if sp.issparse(B) else B
+    B = sp.csc_matrix(B)
     fy = ~ay
-    BF = Bd[:, fy]
-    K = (BF / w[fy]) @ BF.T
+    BF = B[:, np.flatnonzero(fy)]
+    K = (BF @ sp.diags(1.0 / w[fy]) @ BF.T).toarray()
     K[np.diag_indices(N)] += np.where(au, 0.0, psi * psi / (p.gamma * w))
-    rhs = BF @ ybar[fy] + Bd[:, ay] @ yA[ay] + psi * np.where(au, uA, 0.0) - psi * g
-    pv = sla.solve(K, rhs, assume_a="pos")
-    BTp = Bd.T @ pv
+    rhs = BF @ ybar[fy] + B[:, np.flatnonzero(ay)] @ yA[ay] + psi * np.where(au, uA, 0.0) - psi * g
+    try:
+        pv = sla.solve(K, rhs, assume_a="pos")
+    except (np.linalg.LinAlgError, sla.LinAlgError):
+        # an intermediate active set of active_set_solve can make K singular
+        pv = sla.lstsq(K, rhs)[0]
+    BTp = B.T @ pv
     y = np.where(ay, yA, ybar - BTp / w)
     u = np.where(au, uA, -psi * pv / (p.gamma * w))
     mu_y = -(w * (y - ybar) + BTp)
@@ -593,3 +597,36 @@ def l2_misfit(p, y, ybar) -> float:
     hx, hy, ht = mesh(p)
     w = objective_weights(p)
     return math.sqrt(hx * hy * ht * float(np.sum(w * (y - ybar) ** 2)))
+
+
+def active_set_solve(inst, max_iter: int = 50) -> KktSolution:
+    """Exact optimum of the box-constrained QP by a primal-dual active-set
+    iteration: starting from the unconstrained solution, a component is taken as
+    active at its upper (lower) bound when mu + c (x - bound) > 0 (< 0), with c
+    the curvature of the objective in that variable (c_y = w, c_u = gamma w /
+    psi for the psi-scaled multiplier of u), and kkt_solve is repeated until the
+    active sets repeat. The KKT conditions of the result are checked by
+    kkt_violation in the tests. Control bounds only (state bounds: use polish)."""
+    if inst.ya is not None or inst.yb is not None:
+        raise NotImplementedError("active_set_solve handles control bounds only")
+    p = inst.params
+    psi = psi_scale(p)
+    w = objective_weights(p)
+    lo_y, hi_y = box_bounds(p, inst.ya, inst.yb)
+    lo_u, hi_u = box_bounds(p, inst.ua, inst.ub)
+    B = assemble_B_sparse(p)
+    none = np.zeros(w.shape, bool)
+    sol = kkt_solve(inst, none, none, none, none, B=B)
+    sets = None
+    for _ in range(max_iter):
+        ay_hi = sol.mu_y + w * (sol.y - hi_y) > 0
+        ay_lo = sol.mu_y + w * (sol.y - lo_y) < 0
+        cu = p.gamma * w / psi
+        au_hi = sol.mu_u + cu * (sol.u - hi_u) > 0
+        au_lo = sol.mu_u + cu * (sol.u - lo_u) < 0
+        new = (ay_lo, ay_hi, au_lo, au_hi)
+        if sets is not None and all(np.array_equal(a, b) for a, b in zip(new, sets)):
+            return sol
+        sets = new
+        sol = kkt_solve(inst, ay_lo, ay_hi, au_lo, au_hi, B=B)
+    return sol

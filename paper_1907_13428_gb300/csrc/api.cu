@@ -685,6 +685,7 @@ struct fde_batch {
   double** y = nullptr;
   double** u = nullptr;
   double* bounds = nullptr;  // 4 per instance: ya, yb, ua, ub
+  long long kernels = 0;     // kernel nodes of the captured graph
 };
 
 extern "C" {
@@ -777,6 +778,7 @@ int fde_batch_admm_solve(fde_batch* b, const fde_admm_opts* o, const double* con
       b->exec = nullptr;
     }
     cudaGraph_t graph = nullptr;
+    const long long before = g_launches.load();
     CK(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
     int status = FDE_OK;
     cudaError_t e = cudaEventRecord(b->fork, b->capture);
@@ -807,9 +809,13 @@ int fde_batch_admm_solve(fde_batch* b, const fde_admm_opts* o, const double* con
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_status(e);
     b->opts = *o;
+    // captured launches did not run; each graph launch runs them all
+    b->kernels = g_launches.load() - before;
+    g_launches.fetch_sub(b->kernels);
   }
   cudaStream_t st = (cudaStream_t)stream;
   CK(cudaGraphLaunch(b->exec, st));
+  note_launches((int)b->kernels);
   CK(cudaStreamSynchronize(st));
   int status = FDE_OK;
   for (int i = 0; i < n; ++i) {

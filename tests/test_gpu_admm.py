@@ -161,3 +161,56 @@ def test_autograd_function_gradients():
     assert relerr(host(ybar.grad), ref["ybar"]) < 1e-7
     for i, k in enumerate(("dp", "dm", "ep", "em")):
         assert abs(float(coef.grad[i]) - ref[k]) <= 1e-6 * max(1.0, abs(ref[k]))
+
+
+def test_gradient_differentiation_workload_32x32x16():
+    """Differentiation workload's operator on 32x32x16 (control box [-1, 1]):
+    converged GPU solve and fde_admm_grad against the oracle's exact optimum,
+    adjoint and envelope gradient stored by tests/golden/make_grad_golden.py."""
+    import json
+    import os
+    need_gpu()
+    F = lib()
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "grad_32x32x16.json")))
+    inst = fi.config_grad_small()
+    prob = F.Problem(inst.params)
+    # delta = 0.1 converges in a few hundred iterations here; the optimum does not depend on it
+    fo = F.AdmmOptions(delta=0.1, rho=1.618, tol_admm=1e-11, max_admm=50000, inner_tol_mode=1, inner_tol=1e-13)
+    ybar = dev(inst.ybar)
+    r = prob.admm_solve(fo, ybar, ua=inst.ua, ub=inst.ub)
+    assert r["status"] == F.FDE_OK
+    assert abs(r["stats"]["objective"] - g["J"]) <= 1e-8 * abs(g["J"])
+    idx = np.array(g["index"])
+    y = host(r["y"])[idx]
+    assert np.max(np.abs(y - np.array(g["y"]))) <= 1e-8 * g["y_maxabs"]
+    dJ, coef, pv = prob.admm_grad(r["y"], ybar, tol=1e-14)
+    assert np.max(np.abs(host(dJ)[idx] - np.array(g["dJ_dybar"]))) <= 1e-8 * g["y_maxabs"]
+    assert np.max(np.abs(host(pv)[idx] - np.array(g["p"]))) <= 1e-6 * g["p_maxabs"]
+    for a, b in zip(coef.tolist(), g["dcoef"]):
+        assert abs(a - b) <= 1e-6 * max(1.0, abs(b)), (a, b)
+    prob.close()
+
+
+def test_gradient_differentiation_workload_full_size_properties():
+    """256x256x64, beta = 1.5: after a fixed-iteration solve the adjoint solve
+    returns p with B^T p = -J1 (y - ybar) (checked with the library's own B^T),
+    and dJ/dybar equals -J1 (y - ybar) computed on the host."""
+    need_gpu()
+    F = lib()
+    inst = fi.config_grad()
+    p = inst.params
+    prob = F.Problem(p)
+    fo = F.AdmmOptions(delta=1.0, rho=1.618, max_admm=3, fixed_iters=True, inner_tol_mode=1, inner_tol=1e-10,
+                       precision=F.FDE_MIXED)
+    ybar = dev(inst.ybar)
+    r = prob.admm_solve(fo, ybar, ua=inst.ua, ub=inst.ub)
+    dJ, coef, pv = prob.admm_grad(r["y"], ybar, tol=1e-11)
+    w = np.ones((p.nt, p.nx, p.ny))
+    w[-1] = 0.5
+    expect = -(w.ravel() * (host(r["y"]) - inst.ybar.ravel()))
+    assert relerr(host(dJ), expect) < 1e-14
+    btp = host(prob.matvec(pv, F.FDE_OP_BT))
+    assert relerr(btp, expect) < 1e-8
+    assert np.all(np.isfinite(coef.numpy()))
+    prob.close()
+    torch.cuda.empty_cache()

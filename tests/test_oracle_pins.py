@@ -432,3 +432,15 @@ def test_input_generator_is_reproducible_and_standard_normal():
     assert abs(a.mean()) < 0.01 and abs(a.std() - 1.0) < 0.01
     # splitmix64 reference values for seed 0 (published test vector)
     assert int(fi.splitmix64(0, 1)[0]) == 0xE220A8397B1DCDAF
+
+
+@pytest.mark.parametrize("boxes", [dict(ua=-0.05, ub=0.05), dict(ua=-0.2, ub=0.02), dict(ua=-1e3, ub=1e3),
+                                   dict(ua=0.0, ub=0.1)])
+def test_active_set_solve_is_the_admm_limit(boxes):
+    inst = _tiny_instance(nx=5, ny=4, nt=3, **boxes)
+    sol = O.active_set_solve(inst)
+    v = O.kkt_violation(inst, sol)
+    assert v["equality"] < 1e-10 and v["box"] < 1e-12 and v["sign_complementarity"] < 1e-8, v
+    st = O.admm_direct(inst, O.AdmmOptions(delta=1.0, rho=1.618, tol=1e-11, max_iter=50000))
+    assert np.allclose(st.y, sol.y, atol=1e-8) and np.allclose(st.u, sol.u, atol=1e-8)
+    assert np.allclose(st.p, sol.p, atol=1e-7)
