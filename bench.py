@@ -39,16 +39,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "medium", "small", "batch"])
+    ap.add_argument("--workload", default="large", choices=["large", "medium", "small", "slab", "batch"])
     ap.add_argument("--admm-iters", type=int, default=3)
     ap.add_argument("--sub-tol", type=float, default=1e-8)
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 comparison, e2e and CPU baseline")
+    ap.add_argument("--kernels", action="store_true",
+                    help="only time the single-launch transform passes of the workload (profiling command)")
     return ap.parse_args()
 
 
 def workload(name):
     import fde_inputs as fi
-    return {"large": fi.config_large, "medium": fi.config_medium, "small": fi.config_small}[name]()
+    return {"large": fi.config_large, "medium": fi.config_medium, "small": fi.config_small,
+            "slab": fi.config_large_slab}[name]()
 
 
 def describe(inst, admm_iters, sub_tol):
@@ -61,6 +64,24 @@ def describe(inst, admm_iters, sub_tol):
         "delta": 1.0, "rho": 1.618, "precision": "mixed (float FFT operator/preconditioner, double refinement)",
         "l2": "no flush: every vector (8N bytes = %.2f GB) exceeds the 126 MB L2" % (8 * p.N / 1e9),
     }
+
+
+def traffic_for(name):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, or None
+    when the kernel sources changed since the capture (hash mismatch)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        h = hashlib.sha256()
+        for fn in d["sources"]:
+            with open(os.path.join(ROOT, fn), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != d["sources_sha256"]:
+            return None
+        return d["kernels"][name]["bytes_per_launch_full_size"]
+    except Exception:
+        return None
 
 
 def peaks():
@@ -251,16 +272,37 @@ def run_ours(args):
         t_m32 = evtime(lambda: prob.precond(x32, mixed, out=y32))
         t_b64 = evtime(lambda: prob.matvec(ybar, F.FDE_OP_B, out=y64), reps=3)
         t_m64 = evtime(lambda: prob.precond(ybar, mixed, out=y64), reps=3)
+        # single launches: one Kronecker factor per call (x2 pass = k_rows_reg, x1 pass = k_axis_reg)
+        t_x2_64 = evtime(lambda: prob.apply_factor(ybar, 2, out=y64), reps=3)
+        t_x1_64 = evtime(lambda: prob.apply_factor(ybar, 1, out=y64), reps=3)
+        t_x2_32 = evtime(lambda: prob.apply_factor(x32, 2, out=y32))
+        t_x1_32 = evtime(lambda: prob.apply_factor(x32, 1, out=y32))
         del x32, y32, y64
         hbm, src = peaks()
+        fp64_peak = F.alu_peak(F.FDE_FP64)
+        fp32_peak = F.alu_peak(F.FDE_FP32)
+        # dominant kernel of the mixed solve (launch-list share): the double x2 Toeplitz pass.
+        # Algorithmic flops per point of one pass: 4 transforms of length L per complex
+        # line of two real lines at 5 L log2 L (10 log2 L per point) plus 13 for the
+        # twists, symbol products and the halves' combination.
+        L = 1
+        while L < p.ny:
+            L *= 2
+        flops = (10.0 * math.log2(L) + 13.0) * N
+        achieved = flops / (t_x2_64 * 1e-3) / 1e12
+        extras["roofline"] = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                              "frac": achieved / fp64_peak, "traffic": traffic_for("k_rows_reg_double_1024"),
+                              "kernel": "k_rows_reg<double,1024>: x2 Toeplitz pass in double (one launch)",
+                              "flops_per_launch": flops, "ms": t_x2_64,
+                              "peak_source": "measured: fde_alu_peak_probe FMA chains, double"}
         alg = 8.0 * N  # read x, write y (float)
-        achieved = alg / (t_b32 * 1e-3) / 1e9
-        extras["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                              "frac": achieved / hbm, "traffic": None,
-                              "kernel": "Toeplitz-FFT matvec y = B x, float (x2 pass + x1 pass)",
-                              "peak_source": src, "ms": t_b32}
+        extras["matvec"] = {"kernel": "Toeplitz-FFT matvec y = B x, float (x1 pass + x2 pass)", "ms": t_b32,
+                            "alg_bytes": alg, "gbs": alg / (t_b32 * 1e-3) / 1e9, "hbm_peak": hbm,
+                            "hbm_frac": alg / (t_b32 * 1e-3) / 1e9 / hbm, "hbm_peak_source": src,
+                            "alu_tflops": 2 * flops / (t_b32 * 1e-3) / 1e12, "fp32_peak_tflops": fp32_peak}
         extras["operators_ms"] = {"B_f32": t_b32, "S_f32": t_s32, "precond_f32": t_m32, "B_f64": t_b64,
-                                  "precond_f64": t_m64}
+                                  "precond_f64": t_m64, "x2_pass_f64": t_x2_64, "x1_pass_f64": t_x1_64,
+                                  "x2_pass_f32": t_x2_32, "x1_pass_f32": t_x1_32}
         # all-FP64 solve with the same iteration count and sub-solve tolerance
         fp64 = F.AdmmOptions(**{**mixed.__dict__, "precision": F.FDE_FP64})
         torch.cuda.synchronize()
@@ -378,10 +420,43 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+def run_kernels(args):
+    """Single launches of the transform passes on the workload (double and float,
+    x2 and x1 factors): the command profiled for the roofline's traffic."""
+    import torch
+
+    import paper_1907_13428_gb300 as F
+    inst = workload(args.workload)
+    prob = F.Problem(inst.params)
+    x64 = torch.as_tensor(inst.ybar.ravel(), device="cuda")
+    x32 = x64.float()
+    y64 = torch.empty_like(x64)
+    y32 = torch.empty_like(x32)
+    out = {}
+    for name, fn in (("x2_pass_f64", lambda: prob.apply_factor(x64, 2, out=y64)),
+                     ("x1_pass_f64", lambda: prob.apply_factor(x64, 1, out=y64)),
+                     ("x2_pass_f32", lambda: prob.apply_factor(x32, 2, out=y32)),
+                     ("x1_pass_f32", lambda: prob.apply_factor(x32, 1, out=y32))):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(max(1, args.steps)):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        out[name] = a.elapsed_time(b) / max(1, args.steps)
+    print(json.dumps({"kernels_ms": out, "workload": describe(inst, 0, 0)["workload"], "N": prob.N}), flush=True)
+    prob.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.kernels:
+        run_kernels(args)
     elif args.workload == "batch":
         run_batch(args)
     else:

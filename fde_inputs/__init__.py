@@ -159,6 +159,14 @@ def config_large() -> FdeInstance:
     return FdeInstance(p, desired_state_sine(p, MASTER_SEED), None, None, None, -1.0, 1.0, MASTER_SEED)
 
 
+def config_large_slab() -> FdeInstance:
+    """The 1024x1024 operator of config_large on 16 time steps (profiling case:
+    the same transform lengths, vectors larger than L2, a few GB on the device)."""
+    inst = config_large()
+    p = FdeParams(**{**inst.params.__dict__, "nt": 16})
+    return FdeInstance(p, desired_state_sine(p, MASTER_SEED), None, None, None, -1.0, 1.0, MASTER_SEED)
+
+
 def config_grad() -> FdeInstance:
     """256x256 x 64 steps, beta = 1.5 on both axes, control box [-1, 1]."""
     p = FdeParams(nx=256, ny=256, nt=64, T=1.0, beta_x=1.5, beta_y=1.5, alpha_t=1.0,

@@ -136,6 +136,13 @@ double fde_psi(const fde_problem* prob);
 int fde_matvec(fde_problem* prob, int op, const fde_admm_opts* opts, int precision,
                const void* x, void* y, void* stream);
 
+/* One Kronecker factor of B alone, one kernel launch: axis 1: y = -psi (I (x) X (x) I) x,
+ * axis 2: y = -psi (I (x) I (x) Y) x, with X = d+ L_x + d- L_x^T and Y = e+ L_y + e- L_y^T
+ * (Eq. FDE constraint matrix); op FDE_OP_BT applies the transposed factor. No
+ * time term. precision FDE_FP64 (double*) or FDE_FP32 (float*); x and y must
+ * not overlap. Errors: FDE_EINVAL. */
+int fde_apply_factor(fde_problem* prob, int axis, int op, int precision, const void* x, void* y, void* stream);
+
 /* Preconditioner z = S~^-1 r with S~ = m1 I + C_3(B)^T C_3(B) / m2 (Eq. first
  * schur complement preconditioner with C_3 of Eq. multilevel circulant
  * preconditioner, J replaced by I): FFT, divide by m1 + |Lambda|^2/m2,
@@ -229,6 +236,12 @@ long long fde_batch_instance_size(const fde_batch* batch, int i);
 int fde_batch_admm_solve(fde_batch* batch, const fde_admm_opts* opts, const double* const* ybar,
                          const double* ya, const double* yb, const double* ua, const double* ub,
                          double* const* y, double* const* u, fde_admm_stats* stats, void* stream);
+
+/* Arithmetic peak of this GPU measured with independent fused multiply-add
+ * chains (precision FDE_FP64 or FDE_FP32), in TFLOP/s, best of three runs of
+ * about 70 ms (double) or 5 ms (float); a diagnostic used as the roofline of
+ * the arithmetic-bound double transforms. Synchronises `stream`. */
+int fde_alu_peak_probe(int precision, double* tflops, void* stream);
 
 /* Static message for a status code. */
 const char* fde_strerror(int status);

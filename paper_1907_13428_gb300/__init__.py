@@ -63,6 +63,8 @@ _SIGS = {
     "fde_last_cuda_error": (ctypes.c_char_p, []),
     "fde_kernel_launches": (ctypes.c_longlong, []),
     "fde_matvec_noalloc": (ctypes.c_int, [ctypes.POINTER(fde_params), ctypes.c_int, _P, _P, _P]),
+    "fde_apply_factor": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+    "fde_alu_peak_probe": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
     "fde_batch_setup": (ctypes.c_int, [ctypes.POINTER(fde_params), ctypes.c_int, ctypes.POINTER(_P), _P]),
     "fde_batch_destroy": (None, [_P]),
     "fde_batch_instance_size": (ctypes.c_longlong, [_P, ctypes.c_int]),
@@ -92,6 +94,13 @@ def lib() -> ctypes.CDLL:
 def kernel_launches() -> int:
     """Kernel launches issued by the library so far in this process."""
     return int(lib().fde_kernel_launches())
+
+
+def alu_peak(precision: int = FDE_FP64) -> float:
+    """Measured fused-multiply-add peak of the current GPU in TFLOP/s."""
+    v = ctypes.c_double()
+    _check(lib().fde_alu_peak_probe(precision, ctypes.byref(v), _stream()), "fde_alu_peak_probe")
+    return v.value
 
 
 class FdeError(RuntimeError):
@@ -186,6 +195,14 @@ class Problem:
         o = (opts or AdmmOptions()).c()
         _check(lib().fde_matvec(self._h, op, ctypes.byref(o), prec, _ptr(x, None, self.N), _ptr(y, x.dtype, self.N),
                                 _stream()), "fde_matvec")
+        return y
+
+    def apply_factor(self, x: torch.Tensor, axis: int, op: int = FDE_OP_B, out=None) -> torch.Tensor:
+        """One Kronecker factor of B along x1 (axis 1) or x2 (axis 2): one kernel launch."""
+        prec = FDE_FP64 if x.dtype == torch.float64 else FDE_FP32
+        y = torch.empty_like(x) if out is None else out
+        _check(lib().fde_apply_factor(self._h, axis, op, prec, _ptr(x, None, self.N), _ptr(y, x.dtype, self.N),
+                                      _stream()), "fde_apply_factor")
         return y
 
     def precond(self, r: torch.Tensor, opts: Optional[AdmmOptions] = None,

@@ -92,7 +92,10 @@ AdmmArgs make_admm_args(fde_problem* P, const fde_admm_opts* o, const Diags& dg,
     A.w[s] = dg.w.v[s];
     A.Q[s] = dg.Q.v[s];
     A.M2[s] = dg.M2.v[s];
+    A.inv_Q[s] = 1.0 / dg.Q.v[s];
+    A.inv_M2[s] = 1.0 / dg.M2.v[s];
   }
+  A.delta_over_psi = o->delta / P->psi;
   A.ybar = ybar;
   A.g = g;
   A.ya = ya;
@@ -417,6 +420,20 @@ int fde_matvec(fde_problem* P, int op, const fde_admm_opts* o, int precision, co
       return op_S<float>(P, dg, (const float*)x, (float*)y, s, st);
     }
     CK(apply_B<float>(P, op == FDE_OP_BT, (const float*)x, (float*)y, nullptr, nullptr, nullptr, s.t1, s.t2, st));
+  }
+  return FDE_OK;
+}
+
+int fde_apply_factor(fde_problem* P, int axis, int op, int precision, const void* x, void* y, void* stream) {
+  if (!P || !x || !y || x == y || (axis != 1 && axis != 2) || (op != FDE_OP_B && op != FDE_OP_BT)) return FDE_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int conj = op == FDE_OP_BT;
+  if (precision == FDE_FP64) {
+    CK(apply_axis_raw<double>(P, axis, (const double*)x, (double*)y, P->ax[axis].d.sym, conj, st));
+  } else if (precision == FDE_FP32) {
+    CK(apply_axis_raw<float>(P, axis, (const float*)x, (float*)y, P->ax[axis].f.sym, conj, st));
+  } else {
+    return FDE_EINVAL;
   }
   return FDE_OK;
 }

@@ -368,6 +368,7 @@ template cudaError_t apply_S<float>(fde_problem*, const SliceDiag&, const SliceD
                                     float*, float*, cudaStream_t, Gate);
 template cudaError_t apply_axis_raw<double>(fde_problem*, int, const double*, double*, const double2*, int,
                                             cudaStream_t);
+template cudaError_t apply_axis_raw<float>(fde_problem*, int, const float*, float*, const float2*, int, cudaStream_t);
 
 }  // namespace fde
 

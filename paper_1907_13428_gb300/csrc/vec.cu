@@ -230,15 +230,16 @@ __global__ void k_admm_pre(const AdmmArgs A, double* __restrict__ c, double* __r
                            double* __restrict__ q) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.n; i += (long long)gridDim.x * blockDim.x) {
     const int last = (i >= A.last_start);
-    const double w = A.w[last], Q = A.Q[last], M2 = A.M2[last];
+    // reciprocals instead of divides: double divides are slow on this GPU
+    const double w = A.w[last], iQ = A.inv_Q[last], iM2 = A.inv_M2[last];
     const double p = A.p[i];
     const double gi = A.g ? A.g[i] : 0.0;
     c[i] = A.rho * (w * A.ybar[i] - A.wy[i] + A.zy[i] * A.inv_delta);
     const double b = A.rho * (-A.psi * A.wu[i] + A.psi * A.psi * A.zu[i] * A.inv_delta) + (1.0 - A.rho) * A.psi * p;
     bu[i] = b;
-    const double r = A.psi * b / Q - A.psi * gi + A.delta_over_rho * p;
+    const double r = A.psi * b * iQ - A.psi * gi + A.delta_over_rho * p;
     r0[i] = r;
-    q[i] = (1.0 - A.rho) * p - r / M2;
+    q[i] = (1.0 - A.rho) * p - r * iM2;
   }
 }
 
@@ -258,14 +259,14 @@ __global__ void __launch_bounds__(kRedThreads) k_admm_post(const AdmmArgs A, con
   bool bad = false;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.n; i += (long long)gridDim.x * blockDim.x) {
     const int last = (i >= A.last_start);
-    const double w = A.w[last], Q = A.Q[last], M2 = A.M2[last];
+    const double w = A.w[last], iQ = A.inv_Q[last], iM2 = A.inv_M2[last];
     const double yi = y[i], byi = By[i];
-    const double p = (byi + r0[i]) / M2;
-    const double ui = (bu[i] - A.psi * p) / Q;
+    const double p = (byi + r0[i]) * iM2;
+    const double ui = (bu[i] - A.psi * p) * iQ;
     const double lo_y = A.ya ? A.ya[i] : A.ya_s, hi_y = A.yb ? A.yb[i] : A.yb_s;
     const double lo_u = A.ua ? A.ua[i] : A.ua_s, hi_u = A.ub ? A.ub[i] : A.ub_s;
     const double zy = fmin(fmax(yi + A.delta * A.wy[i], lo_y), hi_y);
-    const double zu = fmin(fmax(ui + A.delta * A.wu[i] / A.psi, lo_u), hi_u);
+    const double zu = fmin(fmax(ui + A.delta_over_psi * A.wu[i], lo_u), hi_u);
     A.wy[i] += A.rho_over_delta * (yi - zy);
     A.wu[i] += A.rho_over_delta * A.psi * (ui - zu);
     A.zy[i] = zy;

@@ -21,6 +21,7 @@ struct AdmmArgs {
   long long n, last_start;           // last_start = (nt-1)*nx*ny: first index of the last slice
   double rho, delta, inv_delta, rho_over_delta, delta_over_rho, psi, gamma;
   double w[2], Q[2], M2[2];          // slice-constant diagonals (0: slices < nt-1, 1: last slice)
+  double inv_Q[2], inv_M2[2], delta_over_psi;
   const double* ybar;
   const double* g;                   // nullable
   const double *ya, *yb, *ua, *ub;   // nullable

@@ -139,3 +139,30 @@ def test_matvec_full_size_sampled(cfg):
         del full, full32
     prob.close()
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dims", [(7, 5, 3), (33, 17, 4), (64, 128, 2)])
+def test_apply_factor_single_axis(dims):
+    """fde_apply_factor: one Kronecker factor, -psi X along x1 or -psi Y along x2."""
+    need_gpu()
+    F = lib()
+    nx, ny, nt = dims
+    p = params(nx, ny, nt)
+    prob = F.Problem(p)
+    x = fi.random_field(21, (nt, nx, ny))
+    X, Y = O.space_matrices(p)
+    psi = O.psi_scale(p)
+    for axis, M, along in ((1, X, O.along_x1), (2, Y, O.along_x2)):
+        for op, Mt in ((F.FDE_OP_B, M), (F.FDE_OP_BT, M.T)):
+            ref = -psi * along(Mt, x)
+            assert relerr(host(prob.apply_factor(dev(x), axis, op)), ref) < 1e-12
+            assert relerr(host(prob.apply_factor(dev(x, torch.float32), axis, op)), ref) < 2e-5
+    prob.close()
+
+
+def test_alu_peak_probe_is_plausible():
+    need_gpu()
+    F = lib()
+    f64 = F.alu_peak(F.FDE_FP64)
+    f32 = F.alu_peak(F.FDE_FP32)
+    assert 0.1 < f64 < 200 and 1 < f32 < 500 and f32 > f64
