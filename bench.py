@@ -213,6 +213,7 @@ def run_ours(args):
     inst = workload(args.workload)
     p = inst.params
     prob = F.Problem(p)
+    tiles = prob.autotune()  # float FFT tiles picked by timing on this problem
     N = prob.N
     ybar = torch.as_tensor(inst.ybar.ravel(), device=dev)
     bounds = dict(ya=inst.ya, yb=inst.yb, ua=inst.ua, ub=inst.ub)
@@ -344,7 +345,8 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": describe(inst, args.admm_iters, args.sub_tol), "gpu_launches": launches,
+                "config": {**describe(inst, args.admm_iters, args.sub_tol), "fft_tiles_threads": tiles},
+                "gpu_launches": launches,
                 "clocks": clk.summary(), "solve_stats": stats}
         line.update(extras)
         print(json.dumps(line), flush=True)

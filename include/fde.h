@@ -143,6 +143,16 @@ int fde_matvec(fde_problem* prob, int op, const fde_admm_opts* opts, int precisi
  * not overlap. Errors: FDE_EINVAL. */
 int fde_apply_factor(fde_problem* prob, int axis, int op, int precision, const void* x, void* y, void* stream);
 
+/* FFT tile autotuning: times the float transform passes of this problem with
+ * each tile configuration (threads per CTA, hence lines per CTA) on the
+ * problem's own sizes and keeps the fastest for all later float products of
+ * `prob`. Without it a fixed default is used. fde_batch_setup calls it for
+ * every instance. Synchronises `stream`. Errors: FDE_EINVAL, FDE_ECUDA. */
+int fde_autotune(fde_problem* prob, void* stream);
+
+/* Current tile choice: threads per CTA of the float x2 pass and x1 pass. */
+int fde_tiles(const fde_problem* prob, int* rows_threads, int* axis_threads);
+
 /* Preconditioner z = S~^-1 r with S~ = m1 I + C_3(B)^T C_3(B) / m2 (Eq. first
  * schur complement preconditioner with C_3 of Eq. multilevel circulant
  * preconditioner, J replaced by I): FFT, divide by m1 + |Lambda|^2/m2,

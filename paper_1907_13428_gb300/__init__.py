@@ -65,6 +65,8 @@ _SIGS = {
     "fde_matvec_noalloc": (ctypes.c_int, [ctypes.POINTER(fde_params), ctypes.c_int, _P, _P, _P]),
     "fde_apply_factor": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
     "fde_alu_peak_probe": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
+    "fde_autotune": (ctypes.c_int, [_P, _P]),
+    "fde_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "fde_batch_setup": (ctypes.c_int, [ctypes.POINTER(fde_params), ctypes.c_int, ctypes.POINTER(_P), _P]),
     "fde_batch_destroy": (None, [_P]),
     "fde_batch_instance_size": (ctypes.c_longlong, [_P, ctypes.c_int]),
@@ -196,6 +198,16 @@ class Problem:
         _check(lib().fde_matvec(self._h, op, ctypes.byref(o), prec, _ptr(x, None, self.N), _ptr(y, x.dtype, self.N),
                                 _stream()), "fde_matvec")
         return y
+
+    def autotune(self):
+        """Pick the float FFT tiles by timing (fde_autotune); returns (rows, axis) threads."""
+        _check(lib().fde_autotune(self._h, _stream()), "fde_autotune")
+        return self.tiles()
+
+    def tiles(self):
+        a, c = ctypes.c_int(), ctypes.c_int()
+        _check(lib().fde_tiles(self._h, ctypes.byref(a), ctypes.byref(c)), "fde_tiles")
+        return a.value, c.value
 
     def apply_factor(self, x: torch.Tensor, axis: int, op: int = FDE_OP_B, out=None) -> torch.Tensor:
         """One Kronecker factor of B along x1 (axis 1) or x2 (axis 2): one kernel launch."""

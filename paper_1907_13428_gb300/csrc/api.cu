@@ -424,6 +424,19 @@ int fde_matvec(fde_problem* P, int op, const fde_admm_opts* o, int precision, co
   return FDE_OK;
 }
 
+int fde_autotune(fde_problem* P, void* stream) {
+  if (!P) return FDE_EINVAL;
+  CK(autotune_tiles(P, P->v32[F_W], P->v32[F_T1], (cudaStream_t)stream));
+  return FDE_OK;
+}
+
+int fde_tiles(const fde_problem* P, int* rows_threads, int* axis_threads) {
+  if (!P || !rows_threads || !axis_threads) return FDE_EINVAL;
+  *rows_threads = P->rows_nt32;
+  *axis_threads = P->axis_nt32;
+  return FDE_OK;
+}
+
 int fde_apply_factor(fde_problem* P, int axis, int op, int precision, const void* x, void* y, void* stream) {
   if (!P || !x || !y || x == y || (axis != 1 && axis != 2) || (op != FDE_OP_B && op != FDE_OP_BT)) return FDE_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
@@ -750,6 +763,12 @@ int fde_batch_setup(const fde_params* params, int count, fde_batch** out, void* 
         fde_batch_destroy(b);
         return FDE_EUNSUPPORTED;
       }
+    // FFT tiles of every instance picked by timing on its own sizes
+    const int t = fde_autotune(b->probs[i], stream);
+    if (t != FDE_OK) {
+      fde_batch_destroy(b);
+      return t;
+    }
     cudaError_t e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {

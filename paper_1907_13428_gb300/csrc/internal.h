@@ -71,6 +71,9 @@ struct fde_problem {
   int npartials = 0;
   void* allocs[96] = {};
   int nallocs = 0;
+  // FFT tile choice of the float register kernels (threads per CTA), set by fde_autotune
+  int rows_nt32 = 256;  // x2 pass: 128 or 256 (row pairs per CTA = threads / (L/16))
+  int axis_nt32 = 512;  // x1 / t pass: 256 or 512 (column pairs per CTA = threads / (L/16))
 };
 
 namespace fde {
@@ -118,6 +121,10 @@ cudaError_t apply_S(fde_problem* P, const SliceDiag& M1, const SliceDiag& M2inv,
 template <typename R>
 cudaError_t apply_axis_raw(fde_problem* P, int axis, const R* x, R* y, const cplx<R>* sym, int conj_sym,
                            cudaStream_t st);
+
+// Times the float tile variants of the x2 and x1 passes on this problem (x, y:
+// scratch float vectors of length N) and keeps the fastest in P (toeplitz.cu).
+cudaError_t autotune_tiles(fde_problem* P, const float* x, float* y, cudaStream_t st);
 
 // Preconditioner (precond.cu): z = S~^-1 r (r and z may alias). mode 0: S~
 // (m1, m2); mode 1: (C3 C3^T)^-1 (the adjoint normal-equation preconditioner).

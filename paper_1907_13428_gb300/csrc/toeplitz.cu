@@ -217,7 +217,7 @@ cudaError_t launch_rows_reg(fde_problem* P, const R* x, int conj_sym, const cplx
 template <typename R>
 cudaError_t launch_axis_reg(int L, const R* x, int n, long long axis_stride, long long n_inner,
                             long long outer_stride, long long n_outer, const cplx<R>* sym, const AxisTables<R>& T,
-                            int conj_sym, const AxisEpi<R>& E, cudaStream_t st);
+                            int conj_sym, const AxisEpi<R>& E, int nt_choice, cudaStream_t st);
 cudaError_t toeplitz_reg_set_smem_attrs();
 
 template <typename R> static const AxisTables<R>& tables(const Axis& A);
@@ -272,7 +272,7 @@ static cudaError_t launch_axis(fde_problem* P, int axis, const R* x, int conj_sy
   }
   if (L >= 16)
     return launch_axis_reg<R>(L, x, A.n, axis_stride, n_inner, outer_stride, n_outer, sym ? sym : T.sym, T, conj_sym,
-                              E, st);
+                              E, P->axis_nt32, st);
   const long long total = n_outer * ((n_inner + 1) / 2);
   if (pairs > total) pairs = (int)total;
   const long long grid = (total + pairs - 1) / pairs;
@@ -538,11 +538,11 @@ __global__ void __launch_bounds__(NT) k_axis_reg(const R* __restrict__ x, int n,
 template <typename R> constexpr int rows_nt() { return 256; }
 template <typename R> constexpr int axis_nt() { return sizeof(R) == 4 ? 512 : 256; }
 
-template <typename R, int L>
-static cudaError_t launch_rows_reg_L(fde_problem* P, const R* x, int conj_sym, const cplx<R>* sym,
-                                     const AxisTables<R>& T, const AxisEpi<R>& E, cudaStream_t st) {
-  constexpr int NT = rows_nt<R>();
+template <typename R, int L, int NT>
+static cudaError_t launch_rows_reg_LN(fde_problem* P, const R* x, int conj_sym, const cplx<R>* sym,
+                                      const AxisTables<R>& T, const AxisEpi<R>& E, cudaStream_t st) {
   constexpr int PAIRS = NT / (L / 16);
+  static_assert(PAIRS >= 1, "at least one row pair per CTA");
   const long long nrows = (long long)P->nt * P->nx;
   const long long npairs = (nrows + 1) / 2;
   const long long grid = (npairs + PAIRS - 1) / PAIRS;
@@ -552,12 +552,22 @@ static cudaError_t launch_rows_reg_L(fde_problem* P, const R* x, int conj_sym, c
   return cudaGetLastError();
 }
 
+// float: the tile chosen by fde_autotune (128 or 256 threads); double: 256
 template <typename R, int L>
-static cudaError_t launch_axis_reg_L(const R* x, int n, long long axis_stride, long long n_inner,
-                                     long long outer_stride, long long n_outer, const cplx<R>* sym,
-                                     const AxisTables<R>& T, int conj_sym, const AxisEpi<R>& E, cudaStream_t st) {
-  constexpr int NT = axis_nt<R>();
+static cudaError_t launch_rows_reg_L(fde_problem* P, const R* x, int conj_sym, const cplx<R>* sym,
+                                     const AxisTables<R>& T, const AxisEpi<R>& E, cudaStream_t st) {
+  if constexpr (sizeof(R) == 4 && L <= 2048) {
+    if (P->rows_nt32 == 128) return launch_rows_reg_LN<R, L, 128>(P, x, conj_sym, sym, T, E, st);
+  }
+  return launch_rows_reg_LN<R, L, rows_nt<R>()>(P, x, conj_sym, sym, T, E, st);
+}
+
+template <typename R, int L, int NT>
+static cudaError_t launch_axis_reg_LN(const R* x, int n, long long axis_stride, long long n_inner,
+                                      long long outer_stride, long long n_outer, const cplx<R>* sym,
+                                      const AxisTables<R>& T, int conj_sym, const AxisEpi<R>& E, cudaStream_t st) {
   constexpr int CP = NT / (L / 16);
+  static_assert(CP >= 1, "at least one column pair per CTA");
   const long long total = n_outer * ((n_inner + 1) / 2);
   const long long grid = (total + CP - 1) / CP;
   const size_t smem = (size_t)L * 2 * CP * sizeof(cplx<R>);
@@ -568,6 +578,20 @@ static cudaError_t launch_axis_reg_L(const R* x, int n, long long axis_stride, l
                                                          T.tw2, T.twL, conj_sym, E, vec2);
   note_launches(1);
   return cudaGetLastError();
+}
+
+template <typename R, int L>
+static cudaError_t launch_axis_reg_L(const R* x, int n, long long axis_stride, long long n_inner,
+                                     long long outer_stride, long long n_outer, const cplx<R>* sym,
+                                     const AxisTables<R>& T, int conj_sym, const AxisEpi<R>& E, int nt_choice,
+                                     cudaStream_t st) {
+  if constexpr (sizeof(R) == 4) {
+    if (nt_choice == 256)
+      return launch_axis_reg_LN<R, L, 256>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym, E,
+                                           st);
+  }
+  return launch_axis_reg_LN<R, L, axis_nt<R>()>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym,
+                                                E, st);
 }
 
 #define FDE_FOR_EACH_L(M) M(16) M(32) M(64) M(128) M(256) M(512) M(1024) M(2048) M(4096)
@@ -587,12 +611,12 @@ cudaError_t launch_rows_reg(fde_problem* P, const R* x, int conj_sym, const cplx
 template <typename R>
 cudaError_t launch_axis_reg(int L, const R* x, int n, long long axis_stride, long long n_inner,
                             long long outer_stride, long long n_outer, const cplx<R>* sym, const AxisTables<R>& T,
-                            int conj_sym, const AxisEpi<R>& E, cudaStream_t st) {
+                            int conj_sym, const AxisEpi<R>& E, int nt_choice, cudaStream_t st) {
   switch (L) {
 #define FDE_CASE(LL)                                                                                       \
   case LL:                                                                                                 \
     return launch_axis_reg_L<R, LL>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym, E, \
-                                    st);
+                                    nt_choice, st);
     FDE_FOR_EACH_L(FDE_CASE)
 #undef FDE_CASE
     default: return cudaErrorInvalidValue;
@@ -605,9 +629,9 @@ template cudaError_t launch_rows_reg<float>(fde_problem*, const float*, int, con
                                             const AxisTables<float>&, const AxisEpi<float>&, cudaStream_t);
 template cudaError_t launch_axis_reg<double>(int, const double*, int, long long, long long, long long, long long,
                                              const double2*, const AxisTables<double>&, int,
-                                             const AxisEpi<double>&, cudaStream_t);
+                                             const AxisEpi<double>&, int, cudaStream_t);
 template cudaError_t launch_axis_reg<float>(int, const float*, int, long long, long long, long long, long long,
-                                            const float2*, const AxisTables<float>&, int, const AxisEpi<float>&,
+                                            const float2*, const AxisTables<float>&, int, const AxisEpi<float>&, int,
                                             cudaStream_t);
 
 template <typename R>
@@ -627,7 +651,67 @@ static cudaError_t set_attrs_reg() {
 cudaError_t toeplitz_reg_set_smem_attrs() {
   cudaError_t e = set_attrs_reg<float>();
   if (e != cudaSuccess) return e;
-  return set_attrs_reg<double>();
+  if ((e = set_attrs_reg<double>()) != cudaSuccess) return e;
+  const int big = 200 * 1024;
+#define FDE_ATTR2(LL)                                                                                        \
+  if (e == cudaSuccess)                                                                                      \
+    e = cudaFuncSetAttribute(k_axis_reg<float, LL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  FDE_FOR_EACH_L(FDE_ATTR2)
+#undef FDE_ATTR2
+#define FDE_ATTR3(LL)                                                                                        \
+  if (e == cudaSuccess)                                                                                      \
+    e = cudaFuncSetAttribute(k_rows_reg<float, LL, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  FDE_ATTR3(16) FDE_ATTR3(32) FDE_ATTR3(64) FDE_ATTR3(128) FDE_ATTR3(256) FDE_ATTR3(512) FDE_ATTR3(1024)
+  FDE_ATTR3(2048)
+#undef FDE_ATTR3
+  return e;
+}
+
+// Tile autotuning of the float passes: each variant runs three times on the
+// problem's own sizes (after one warm-up launch) and the fastest is kept.
+cudaError_t autotune_tiles(fde_problem* P, const float* x, float* y, cudaStream_t st) {
+  cudaEvent_t a, b;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&a)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&b)) != cudaSuccess) return e;
+  auto time_it = [&](int axis, float* ms) -> cudaError_t {
+    cudaError_t r = apply_axis_raw<float>(P, axis, x, y, P->ax[axis].f.sym, 0, st);
+    if (r != cudaSuccess) return r;
+    cudaEventRecord(a, st);
+    for (int k = 0; k < 3 && r == cudaSuccess; ++k) r = apply_axis_raw<float>(P, axis, x, y, P->ax[axis].f.sym, 0, st);
+    cudaEventRecord(b, st);
+    if (r == cudaSuccess) r = cudaEventSynchronize(b);
+    if (r == cudaSuccess) r = cudaEventElapsedTime(ms, a, b);
+    return r;
+  };
+  float best = 0.f, ms = 0.f;
+  int pick = 256;
+  const int rows_cand[2] = {256, 128};
+  for (int c : rows_cand) {
+    if (c == 128 && P->ax[2].L > 2048) continue;
+    P->rows_nt32 = c;
+    if ((e = time_it(2, &ms)) != cudaSuccess) break;
+    if (c == rows_cand[0] || ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  P->rows_nt32 = pick;
+  const int axis_cand[2] = {512, 256};
+  pick = 512;
+  for (int c : axis_cand) {
+    if (e != cudaSuccess) break;
+    P->axis_nt32 = c;
+    if ((e = time_it(1, &ms)) != cudaSuccess) break;
+    if (c == axis_cand[0] || ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  P->axis_nt32 = pick;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return e;
 }
 
 }  // namespace fde

@@ -166,3 +166,20 @@ def test_alu_peak_probe_is_plausible():
     f64 = F.alu_peak(F.FDE_FP64)
     f32 = F.alu_peak(F.FDE_FP32)
     assert 0.1 < f64 < 200 and 1 < f32 < 500 and f32 > f64
+
+
+@pytest.mark.parametrize("dims", [(64, 64, 8), (128, 256, 4), (33, 1024, 2)])
+def test_autotuned_tiles_keep_parity(dims):
+    """fde_autotune picks valid tiles; products with every tile choice match the oracle."""
+    need_gpu()
+    F = lib()
+    nx, ny, nt = dims
+    p = params(nx, ny, nt)
+    prob = F.Problem(p)
+    rows, axis = prob.autotune()
+    assert rows in (128, 256) and axis in (256, 512)
+    x = fi.random_field(31, (nt, nx, ny))
+    ref = O.apply_B(p, x)
+    assert relerr(host(prob.matvec(dev(x, torch.float32))), ref) < 2e-5
+    assert relerr(host(prob.matvec(dev(x))), ref) < 1e-12
+    prob.close()
