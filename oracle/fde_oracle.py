@@ -27,6 +27,11 @@ Readings of the paper used here (every one is also listed in the design notes):
     (trapezoid, Eq. (discretized Objective function)), or w = 1;
   * preconditioner scalars use J ~ I: m1 = rho (1 + 1/delta),
     m2 = psi^2 / (rho (gamma + psi^2/delta)) + delta/rho;
+  * generalized ADMM (Algorithm 2): both proximal terms carry the factor 1/2
+    (the coefficient matrix printed for R_y = c_y I - J1, R_u = c_u I - J2
+    needs it on the u term too); R_y, R_u positive semi-definite is accepted
+    (c_y >= max w, c_u >= gamma max w), R = 0 being Algorithm 1; the psi-scaled
+    u block is rho (c_u + psi^2/delta); its preconditioner scalars are exact;
   * DFT convention lambda_k = sum_j c_j exp(-2 pi i j k / n) (unnormalised).
 
 Parity status: every function below is pinned by a ``-m "not gpu"`` test in
@@ -193,19 +198,42 @@ def apply_B_at(p, x: np.ndarray, points, transpose: bool = False) -> np.ndarray:
 @dataclasses.dataclass
 class AdmmOptions:
     """delta: penalty parameter (penalty 1/delta); rho: dual step length in
-    (0, (1+sqrt 5)/2); tol: infinity-norm tolerance on the three residuals."""
+    (0, (1+sqrt 5)/2) (Algorithm 1) or (0, 1] (Algorithm 2); tol: infinity-norm
+    tolerance on the three residuals. algorithm 2: generalized ADMM with the
+    proximal matrices R_y = c_y I - J1 and R_u = c_u I - J2 (Section 3.3.2)."""
     delta: float = 1.0
     rho: float = 1.618
     tol: float = 1e-6
     max_iter: int = 1000
+    algorithm: int = 1
+    c_y: float = 0.0
+    c_u: float = 0.0
+
+
+def check_generalized(p, o: AdmmOptions):
+    """Algorithm 2 needs rho in (0, 1] and R_y, R_u positive semi-definite."""
+    w = objective_weights(p)
+    if not (0.0 < o.rho <= 1.0):
+        raise ValueError("generalized ADMM needs rho in (0, 1]")
+    if o.c_y < np.max(w) or o.c_u < p.gamma * np.max(w):
+        raise ValueError("c_y >= max J1 and c_u >= max J2 are required")
 
 
 def admm_diagonals(p, o: AdmmOptions):
-    """M1 = rho (J1 + I/delta), Q = rho (J2 + psi^2 I/delta), M2 = psi^2 Q^-1 + (delta/rho) I."""
+    """M1 = rho (J1 + I/delta), Q = rho (J2 + psi^2 I/delta), M2 = psi^2 Q^-1 + (delta/rho) I.
+    Algorithm 2: J1 + R_y = c_y I and J2 + R_u = c_u I replace J1 and J2
+    (Eq. (generic generalized ADMM subproblems 1and3 optimality operator)), so all
+    three are multiples of the identity."""
     w = objective_weights(p)
     psi = psi_scale(p)
-    M1 = o.rho * (w + 1.0 / o.delta)
-    Q = o.rho * (p.gamma * w + psi * psi / o.delta)
+    if o.algorithm == 2:
+        check_generalized(p, o)
+        one = np.ones_like(w)
+        M1 = o.rho * (o.c_y + 1.0 / o.delta) * one
+        Q = o.rho * (o.c_u + psi * psi / o.delta) * one
+    else:
+        M1 = o.rho * (w + 1.0 / o.delta)
+        Q = o.rho * (p.gamma * w + psi * psi / o.delta)
     M2 = psi * psi / Q + o.delta / o.rho
     return M1, Q, M2
 
@@ -274,8 +302,12 @@ def preconditioner_axis_eigenvalues(p):
 
 
 def preconditioner_scalars(p, o: AdmmOptions):
-    """m1, m2: the scalar (J ~ I) versions of M1 and M2 used in S-tilde."""
+    """m1, m2: the scalar (J ~ I) versions of M1 and M2 used in S-tilde; for
+    Algorithm 2, M1 and M2 themselves (already scalar)."""
     psi = psi_scale(p)
+    if o.algorithm == 2:
+        M1, _, M2 = admm_diagonals(p, o)
+        return float(M1.flat[0]), float(M2.flat[0])
     m1 = o.rho * (1.0 + 1.0 / o.delta)
     m2 = psi * psi / (o.rho * (p.gamma + psi * psi / o.delta)) + o.delta / o.rho
     return m1, m2
@@ -353,12 +385,16 @@ def admm_rhs(p, o, ybar, g, st: AdmmState):
     b_y = rho (J1 ybar - w_y + z_y/delta) + (1-rho) B^T p,
     b_u = rho (-psi w_u + psi^2 z_u/delta) + (1-rho) psi p,
     r0  = psi Q^-1 b_u - psi g + (delta/rho) p,
-    rhs = b_y - B^T (M2^-1 r0)   (right-hand side of S y = rhs)."""
+    rhs = b_y - B^T (M2^-1 r0)   (right-hand side of S y = rhs).
+    Algorithm 2 adds the proximal pulls rho R_y y^j to b_y and rho R_u u^j to b_u."""
     psi = psi_scale(p)
     w = objective_weights(p)
     M1, Q, M2 = admm_diagonals(p, o)
     by = o.rho * (w * ybar - st.wy + st.zy / o.delta) + (1.0 - o.rho) * apply_B(p, st.p, True)
     bu = o.rho * (-psi * st.wu + psi * psi * st.zu / o.delta) + (1.0 - o.rho) * psi * st.p
+    if o.algorithm == 2:
+        by = by + o.rho * (o.c_y - w) * st.y
+        bu = bu + o.rho * (o.c_u - p.gamma * w) * st.u
     r0 = psi * bu / Q - psi * g + (o.delta / o.rho) * st.p
     rhs = by - apply_B(p, r0 / M2, True)
     return rhs, bu, r0
