@@ -379,22 +379,31 @@ def box_bounds(p, lo, hi):
     return lo, hi
 
 
-def admm_rhs(p, o, ybar, g, st: AdmmState):
-    """Right-hand sides of the merged system (the psi-scaled form of Eq. (generic ADMM
-    subproblems 1and3 optimality conditions)) and the pivot quantities:
+def admm_block_rhs(p, o, ybar, g, st: AdmmState):
+    """Right-hand sides of the three block rows of the merged system (the psi-scaled
+    form of Eq. (generic ADMM subproblems 1and3 optimality conditions)):
     b_y = rho (J1 ybar - w_y + z_y/delta) + (1-rho) B^T p,
     b_u = rho (-psi w_u + psi^2 z_u/delta) + (1-rho) psi p,
-    r0  = psi Q^-1 b_u - psi g + (delta/rho) p,
-    rhs = b_y - B^T (M2^-1 r0)   (right-hand side of S y = rhs).
+    f_p = psi g - (delta/rho) p.
     Algorithm 2 adds the proximal pulls rho R_y y^j to b_y and rho R_u u^j to b_u."""
     psi = psi_scale(p)
     w = objective_weights(p)
-    M1, Q, M2 = admm_diagonals(p, o)
     by = o.rho * (w * ybar - st.wy + st.zy / o.delta) + (1.0 - o.rho) * apply_B(p, st.p, True)
     bu = o.rho * (-psi * st.wu + psi * psi * st.zu / o.delta) + (1.0 - o.rho) * psi * st.p
     if o.algorithm == 2:
         by = by + o.rho * (o.c_y - w) * st.y
         bu = bu + o.rho * (o.c_u - p.gamma * w) * st.u
+    fp = psi * g - (o.delta / o.rho) * st.p
+    return by, bu, fp
+
+
+def admm_rhs(p, o, ybar, g, st: AdmmState):
+    """Pivoting the u and p rows of the merged system (Section 3.1):
+    r0  = psi Q^-1 b_u - psi g + (delta/rho) p,
+    rhs = b_y - B^T (M2^-1 r0)   (right-hand side of S y = rhs)."""
+    psi = psi_scale(p)
+    _, Q, M2 = admm_diagonals(p, o)
+    by, bu, _ = admm_block_rhs(p, o, ybar, g, st)
     r0 = psi * bu / Q - psi * g + (o.delta / o.rho) * st.p
     rhs = by - apply_B(p, r0 / M2, True)
     return rhs, bu, r0
@@ -497,6 +506,166 @@ def admm_pcg(inst, o: AdmmOptions, iters: Optional[int] = None, inner_tol: float
         pcg_hist = st.pcg_iters + [k]
         st = admm_after_solve(p, o, g, lo_y, hi_y, lo_u, hi_u, st, y, bu, r0)
         st.pcg_iters = pcg_hist
+        if iters is None and max(st.residuals) <= o.tol:
+            break
+    return st
+
+
+# --------------------------------------------------------------------------
+# Saddle-point sub-problem solved by MINRES with the block-diagonal
+# preconditioner K-tilde (Section 3.3.1, Eq. (generic block-diagonal
+# preconditioner)). Vectors of the 3N system are arrays (3, nt, nx, ny):
+# blocks y, u, p.
+# --------------------------------------------------------------------------
+
+
+def apply_K(p, o: AdmmOptions, x: np.ndarray) -> np.ndarray:
+    """K [y; u; p] with the psi-scaled coefficient matrix of Eq. (generic ADMM
+    subproblems 1and3 optimality conditions):
+    [[M1, 0, B^T], [0, Q, psi I], [B, psi I, -(delta/rho) I]]."""
+    M1, Q, _ = admm_diagonals(p, o)
+    psi = psi_scale(p)
+    y, u, q = (x[k].reshape(p.nt, p.nx, p.ny) for k in range(3))
+    return np.stack([M1 * y + apply_B(p, q, transpose=True),
+                     Q * u + psi * q,
+                     apply_B(p, y) + psi * u - (o.delta / o.rho) * q])
+
+
+def assemble_K(p, o: AdmmOptions) -> np.ndarray:
+    """Dense K (tiny grids)."""
+    M1, Q, _ = admm_diagonals(p, o)
+    B = assemble_B(p)
+    N, psi = p.N, psi_scale(p)
+    Z = np.zeros((N, N))
+    return np.block([[np.diag(M1.ravel()), Z, B.T],
+                     [Z, np.diag(Q.ravel()), psi * np.eye(N)],
+                     [B, psi * np.eye(N), -(o.delta / o.rho) * np.eye(N)]])
+
+
+def schur_p_symbol(p, o: AdmmOptions) -> np.ndarray:
+    """Eigenvalues of Sigma-tilde = m2 I + C_3 C_3^T / m1, the circulant stand-in for
+    the Schur complement (delta/rho) I + B M1^-1 B^T + psi^2 Q^-1 = M2 + B M1^-1 B^T
+    of the p block (m1, m2 as in S-tilde): m2 + |Lambda|^2 / m1."""
+    lt, lx, ly = preconditioner_axis_eigenvalues(p)
+    psi = psi_scale(p)
+    Lam = psi * (lt[:, None, None] - lx[None, :, None] - ly[None, None, :])
+    m1, m2 = preconditioner_scalars(p, o)
+    return m2 + np.abs(Lam) ** 2 / m1
+
+
+def apply_block_preconditioner(p, o: AdmmOptions, r: np.ndarray) -> np.ndarray:
+    """K-tilde^-1 r with K-tilde = blkdiag(M1, Q, Sigma-tilde): J1 and J2 are
+    diagonal, so their blocks are used exactly; Sigma-tilde^-1 by the 3-level DFT."""
+    M1, Q, _ = admm_diagonals(p, o)
+    ry, ru, rq = (r[k].reshape(p.nt, p.nx, p.ny) for k in range(3))
+    Ft, Fx, Fy = dft_matrix(p.nt), dft_matrix(p.nx), dft_matrix(p.ny)
+    R = along_x2(Fy, along_x1(Fx, along_t(Ft, rq.astype(complex))))
+    Z = along_x2(Fy.conj(), along_x1(Fx.conj(), along_t(Ft.conj(), R / schur_p_symbol(p, o)))) / p.N
+    return np.stack([ry / M1, ru / Q, Z.real])
+
+
+def dense_block_preconditioner(p, o: AdmmOptions) -> np.ndarray:
+    """Dense K-tilde with Sigma-tilde assembled from dense T. Chan circulants."""
+    M1, Q, _ = admm_diagonals(p, o)
+    C = caputo_matrix(p)
+    X, Y = space_matrices(p)
+    Ct, Cx, Cy = (circulant(tchan_column(M)) for M in (C, X, Y))
+    It, Ix, Iy = np.eye(p.nt), np.eye(p.nx), np.eye(p.ny)
+    C3 = psi_scale(p) * (np.kron(Ct, np.kron(Ix, Iy)) - np.kron(It, np.kron(Cx, Iy))
+                         - np.kron(It, np.kron(Ix, Cy)))
+    m1, m2 = preconditioner_scalars(p, o)
+    N = p.N
+    Z = np.zeros((N, N))
+    Sig = m2 * np.eye(N) + C3 @ C3.T / m1
+    return np.block([[np.diag(M1.ravel()), Z, Z], [Z, np.diag(Q.ravel()), Z], [Z, Z, Sig]])
+
+
+def minres(apply_A, apply_M, b, x0, tol, max_iter):
+    """Preconditioned MINRES (Paige and Saunders) for symmetric A and symmetric
+    positive definite M: the Lanczos process in the M^-1 inner product builds a
+    tridiagonal T_k, whose QR factorisation by Givens rotations updates x so that
+    ||b - A x||_{M^-1} is minimal over x0 + K_k(M^-1 A, M^-1 r0). The rotations
+    also give that norm, |eta|, at no cost. Stops when |eta| <= tol ||b||_{M^-1}.
+    Returns (x, iterations, |eta| / ||b||_{M^-1})."""
+    x = x0.copy()
+    bn = math.sqrt(max(float(np.vdot(b, apply_M(b)).real), 0.0))
+    if bn == 0.0:
+        return np.zeros_like(b), 0, 0.0
+    v = b - apply_A(x)                      # v_1 (the Lanczos vectors are v_k / beta_k)
+    z = apply_M(v)
+    beta = math.sqrt(max(float(np.vdot(v, z).real), 0.0))
+    eta = beta
+    if eta <= tol * bn:
+        return x, 0, eta / bn
+    v_prev = np.zeros_like(b)
+    beta_prev = 1.0
+    w_prev = np.zeros_like(b)
+    w = np.zeros_like(b)
+    c_prev, c = 1.0, 1.0                    # the two previous rotations
+    s_prev, s = 0.0, 0.0
+    for k in range(1, max_iter + 1):
+        z = z / beta
+        q = apply_A(z)
+        alpha = float(np.vdot(q, z).real)
+        v_next = q - (alpha / beta) * v - (beta / beta_prev) * v_prev
+        z_next = apply_M(v_next)
+        beta_next = math.sqrt(max(float(np.vdot(v_next, z_next).real), 0.0))
+        # column k of T_k: beta_k above the diagonal, alpha_k on it, beta_{k+1} below;
+        # the rotations k-2 and k-1 act on it, a new rotation removes beta_{k+1}
+        e3 = s_prev * beta
+        e2 = s * alpha + c_prev * c * beta
+        e0 = c * alpha - c_prev * s * beta
+        e1 = math.hypot(e0, beta_next)
+        c_new, s_new = e0 / e1, beta_next / e1
+        w_next = (z - e3 * w_prev - e2 * w) / e1
+        x += c_new * eta * w_next
+        eta = -s_new * eta
+        if abs(eta) <= tol * bn:
+            return x, k, abs(eta) / bn
+        v_prev, v = v, v_next
+        beta_prev, beta = beta, beta_next
+        w_prev, w = w, w_next
+        z = z_next
+        c_prev, c = c, c_new
+        s_prev, s = s, s_new
+        if beta == 0.0:                     # invariant subspace: x is exact
+            return x, k, abs(eta) / bn
+    return x, max_iter, abs(eta) / bn
+
+
+def admm_after_saddle(p, o, g, lo_y, hi_y, lo_u, hi_u, st: AdmmState, y, u, pn):
+    """Remaining steps of Algorithm 1 (or 2) given the sub-problem solution (y, u, p)
+    of the saddle-point system: projections and multiplier steps as in admm_after_solve."""
+    psi = psi_scale(p)
+    By = apply_B(p, y)
+    zy = np.clip(y + o.delta * st.wy, lo_y, hi_y)
+    zu = np.clip(u + o.delta * st.wu / psi, lo_u, hi_u)
+    wy = st.wy + (o.rho / o.delta) * (y - zy)
+    wu = st.wu + (o.rho / o.delta) * psi * (u - zu)
+    res = (np.max(np.abs(By + psi * (u - g))), np.max(np.abs(y - zy)), np.max(np.abs(u - zu)))
+    return AdmmState(y, u, zy, zu, pn, wy, wu, st.iters + 1, res, st.pcg_iters)
+
+
+def admm_minres(inst, o: AdmmOptions, iters: Optional[int] = None, inner_tol: float = 1e-10,
+                max_minres: int = 2000) -> AdmmState:
+    """Algorithm 1 (or 2) whose joint (y, u, p) step is the saddle-point system of
+    Eq. (generic ADMM subproblems 1and3 optimality conditions) solved by MINRES with
+    K-tilde (Section 3.3.1), warm-started from the previous (y, u, p)."""
+    p = inst.params
+    g = np.zeros((p.nt, p.nx, p.ny)) if inst.g is None else inst.g
+    lo_y, hi_y = box_bounds(p, inst.ya, inst.yb)
+    lo_u, hi_u = box_bounds(p, inst.ua, inst.ub)
+    st = zero_state(p)
+    A = lambda v: apply_K(p, o, v)
+    M = lambda r: apply_block_preconditioner(p, o, r)
+    n = iters if iters is not None else o.max_iter
+    for _ in range(n):
+        f = np.stack(admm_block_rhs(p, o, inst.ybar, g, st))
+        x0 = np.stack([st.y, st.u, st.p])
+        x, k, _ = minres(A, M, f, x0, inner_tol, max_minres)
+        hist = st.pcg_iters + [k]
+        st = admm_after_saddle(p, o, g, lo_y, hi_y, lo_u, hi_u, st, x[0], x[1], x[2])
+        st.pcg_iters = hist
         if iters is None and max(st.residuals) <= o.tol:
             break
     return st
