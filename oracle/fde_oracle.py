@@ -27,6 +27,9 @@ Readings of the paper used here (every one is also listed in the design notes):
     (trapezoid, Eq. (discretized Objective function)), or w = 1;
   * preconditioner scalars use J ~ I: m1 = rho (1 + 1/delta),
     m2 = psi^2 / (rho (gamma + psi^2/delta)) + delta/rho;
+  * matching Schur approximation (Eq. (second schur complement preconditioner)) with
+    the circulant approximations D-tilde = C_3(B), J1-tilde = J2-tilde = I (Algorithm 1)
+    or the exact scalars (Algorithm 2); it is FFT-diagonal like S-tilde;
   * generalized ADMM (Algorithm 2): both proximal terms carry the factor 1/2
     (the coefficient matrix printed for R_y = c_y I - J1, R_u = c_u I - J2
     needs it on the u term too); R_y, R_u positive semi-definite is accepted
@@ -208,6 +211,7 @@ class AdmmOptions:
     algorithm: int = 1
     c_y: float = 0.0
     c_u: float = 0.0
+    precond: int = 0        # 0: S-tilde (first Schur complement approximation), 1: S-hat (matching)
 
 
 def check_generalized(p, o: AdmmOptions):
@@ -316,12 +320,19 @@ def preconditioner_scalars(p, o: AdmmOptions):
 def preconditioner_symbol(p, o: AdmmOptions) -> np.ndarray:
     """sigma[k, i, j] = m1 + |Lambda|^2 / m2 with Lambda = psi (lambda_t[k] - lambda_x[i]
     - lambda_y[j]), the eigenvalues of C_3(B) (Kronecker sum after Eq. (multilevel
-    circulant preconditioner))."""
+    circulant preconditioner)).
+    Matching variant (o.precond = 1, Eq. (second schur complement preconditioner)) with
+    the circulant D-tilde = C_3(B) and scalar M1, M2: D-hat = C_3^T + sqrt(m1 m2) I is
+    circulant too, so S-hat = D-hat D-hat^T / m2 has the eigenvalues
+    |conj(Lambda) + sqrt(m1 m2)|^2 / m2 = m1 + |Lambda|^2 / m2 + 2 sqrt(m1/m2) Re(Lambda)."""
     lt, lx, ly = preconditioner_axis_eigenvalues(p)
     psi = psi_scale(p)
     Lam = psi * (lt[:, None, None] - lx[None, :, None] - ly[None, None, :])
     m1, m2 = preconditioner_scalars(p, o)
-    return m1 + np.abs(Lam) ** 2 / m2
+    sigma = m1 + np.abs(Lam) ** 2 / m2
+    if o.precond == 1:
+        sigma = sigma + 2.0 * math.sqrt(m1 / m2) * Lam.real
+    return sigma
 
 
 def apply_preconditioner(p, o: AdmmOptions, r: np.ndarray) -> np.ndarray:
@@ -333,6 +344,20 @@ def apply_preconditioner(p, o: AdmmOptions, r: np.ndarray) -> np.ndarray:
     Z = R / preconditioner_symbol(p, o)
     Z = along_x2(Fy.conj(), along_x1(Fx.conj(), along_t(Ft.conj(), Z))) / p.N
     return Z.real
+
+
+def dense_matching_preconditioner(p, o: AdmmOptions) -> np.ndarray:
+    """Dense S-hat = D-hat M2^-1 D-hat^T, D-hat = C_3^T + (m1 m2)^(1/2) I (Eq. (second
+    schur complement preconditioner) with D-tilde = C_3 and the scalar M1, M2)."""
+    C = caputo_matrix(p)
+    X, Y = space_matrices(p)
+    Ct, Cx, Cy = (circulant(tchan_column(M)) for M in (C, X, Y))
+    It, Ix, Iy = np.eye(p.nt), np.eye(p.nx), np.eye(p.ny)
+    C3 = psi_scale(p) * (np.kron(Ct, np.kron(Ix, Iy)) - np.kron(It, np.kron(Cx, Iy))
+                         - np.kron(It, np.kron(Ix, Cy)))
+    m1, m2 = preconditioner_scalars(p, o)
+    Dh = C3.T + math.sqrt(m1 * m2) * np.eye(p.N)
+    return Dh @ Dh.T / m2
 
 
 def dense_preconditioner(p, o: AdmmOptions) -> np.ndarray:
