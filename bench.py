@@ -278,6 +278,9 @@ def run_ours(args):
         t_x1_64 = evtime(lambda: prob.apply_factor(ybar, 1, out=y64), reps=3)
         t_x2_32 = evtime(lambda: prob.apply_factor(x32, 2, out=y32))
         t_x1_32 = evtime(lambda: prob.apply_factor(x32, 1, out=y32))
+        t_bdf = evtime(lambda: prob.matvec(ybar, F.FDE_OP_B, out=y64, dfloat=True), reps=3)
+        t_x2_df = evtime(lambda: prob.apply_factor(ybar, 2, out=y64, dfloat=True), reps=3)
+        t_x1_df = evtime(lambda: prob.apply_factor(ybar, 1, out=y64, dfloat=True), reps=3)
         del x32, y32, y64
         hbm, src = peaks()
         fp64_peak = F.alu_peak(F.FDE_FP64)
@@ -303,7 +306,8 @@ def run_ours(args):
                             "alu_tflops": 2 * flops / (t_b32 * 1e-3) / 1e12, "fp32_peak_tflops": fp32_peak}
         extras["operators_ms"] = {"B_f32": t_b32, "S_f32": t_s32, "precond_f32": t_m32, "B_f64": t_b64,
                                   "precond_f64": t_m64, "x2_pass_f64": t_x2_64, "x1_pass_f64": t_x1_64,
-                                  "x2_pass_f32": t_x2_32, "x1_pass_f32": t_x1_32}
+                                  "x2_pass_f32": t_x2_32, "x1_pass_f32": t_x1_32, "B_df": t_bdf,
+                                  "x2_pass_df": t_x2_df, "x1_pass_df": t_x1_df}
         # all-FP64 solve with the same iteration count and sub-solve tolerance
         fp64 = F.AdmmOptions(**{**mixed.__dict__, "precision": F.FDE_FP64})
         torch.cuda.synchronize()
@@ -318,10 +322,66 @@ def run_ours(args):
         r = step()
         dy = float((out["y"] - y64c).abs().max() / y64c.abs().max())
         du = float((out["u"] - u64c).abs().max() / u64c.abs().max())
-        del y64c, u64c
         extras["fp64_compare"] = {"fp64_solve_s": t64, "mixed_solve_s": value * world, "speedup": t64 / (value * world),
                                   "mixed_vs_fp64_relerr": {"y": dy, "u": du},
                                   "fp64_stats": r64["stats"], "mixed_stats": r["stats"]}
+        # the same solve with double-float refinement products (FDE_MIXED_DF)
+        dfo = F.AdmmOptions(**{**mixed.__dict__, "precision": F.FDE_MIXED_DF})
+        step(dfo)
+        torch.cuda.synchronize()
+        a.record(st)
+        rdf = step(dfo)
+        b.record(st)
+        torch.cuda.synchronize()
+        tdf = a.elapsed_time(b) / 1e3
+        ddy = float((out["y"] - y64c).abs().max() / y64c.abs().max())
+        ddu = float((out["u"] - u64c).abs().max() / u64c.abs().max())
+        # double-float products for the evaluations that cannot be the last, double for the
+        # accepted ones (FDE_MIXED_DFV)
+        dvo = F.AdmmOptions(**{**mixed.__dict__, "precision": F.FDE_MIXED_DFV})
+        step(dvo)
+        torch.cuda.synchronize()
+        a.record(st)
+        rdv = step(dvo)
+        b.record(st)
+        torch.cuda.synchronize()
+        tdv = a.elapsed_time(b) / 1e3
+        extras["dfloat_compare"] = {"mixed_df_solve_s": tdf, "speedup_vs_mixed": value * world / tdf,
+                                    "mixed_df_vs_fp64_relerr": {"y": ddy, "u": ddu}, "mixed_df_stats": rdf["stats"],
+                                    "mixed_dfv_solve_s": tdv, "dfv_speedup_vs_mixed": value * world / tdv,
+                                    "mixed_dfv_vs_fp64_relerr": {
+                                        "y": float((out["y"] - y64c).abs().max() / y64c.abs().max()),
+                                        "u": float((out["u"] - u64c).abs().max() / u64c.abs().max())},
+                                    "mixed_dfv_stats": rdv["stats"]}
+        # the same solve with saddle-point sub-problems by MINRES (Section 3.3.1)
+        mro = F.AdmmOptions(**{**mixed.__dict__, "inner_solver": 1, "max_pcg": 2000})
+        step(mro)
+        torch.cuda.synchronize()
+        a.record(st)
+        rmr = step(mro)
+        b.record(st)
+        torch.cuda.synchronize()
+        tmr = a.elapsed_time(b) / 1e3
+        extras["minres_compare"] = {
+            "mixed_minres_solve_s": tmr, "vs_mixed_pcg": tmr / (value * world),
+            "mixed_minres_vs_fp64_relerr": {"y": float((out["y"] - y64c).abs().max() / y64c.abs().max()),
+                                            "u": float((out["u"] - u64c).abs().max() / u64c.abs().max())},
+            "mixed_minres_stats": rmr["stats"]}
+        # generalized ADMM (Algorithm 2; rho = 1, c_y = 1, c_u = 1.01 gamma) and the matching
+        # Schur approximation S-hat as PCG preconditioner: the same solve otherwise
+        variants = {}
+        for name, kw in (("algorithm2", {"algorithm": 2, "rho": 1.0, "c_y": 1.0, "c_u": 1.01 * p.gamma}),
+                         ("matching_precond", {"precond": 1})):
+            vo = F.AdmmOptions(**{**mixed.__dict__, **kw})
+            step(vo)
+            torch.cuda.synchronize()
+            a.record(st)
+            rv = step(vo)
+            b.record(st)
+            torch.cuda.synchronize()
+            variants[name] = {"solve_s": a.elapsed_time(b) / 1e3, "options": kw, "stats": rv["stats"]}
+        extras["variants"] = variants
+        del y64c, u64c
         # end to end through host buffers: pinned ybar in, y and u out, every step
         hy = torch.empty(N, dtype=torch.float64, pin_memory=True)
         hy.copy_(torch.as_tensor(inst.ybar.ravel()))
@@ -423,8 +483,8 @@ def run_batch(args):
 
 
 def run_kernels(args):
-    """Single launches of the transform passes on the workload (double and float,
-    x2 and x1 factors): the command profiled for the roofline's traffic."""
+    """Single launches of the transform passes on the workload (double, float and
+    double-float; x2 and x1 factors): the command profiled for the roofline's traffic."""
     import torch
 
     import paper_1907_13428_gb300 as F
@@ -438,7 +498,9 @@ def run_kernels(args):
     for name, fn in (("x2_pass_f64", lambda: prob.apply_factor(x64, 2, out=y64)),
                      ("x1_pass_f64", lambda: prob.apply_factor(x64, 1, out=y64)),
                      ("x2_pass_f32", lambda: prob.apply_factor(x32, 2, out=y32)),
-                     ("x1_pass_f32", lambda: prob.apply_factor(x32, 1, out=y32))):
+                     ("x1_pass_f32", lambda: prob.apply_factor(x32, 1, out=y32)),
+                     ("x2_pass_df", lambda: prob.apply_factor(x64, 2, out=y64, dfloat=True)),
+                     ("x1_pass_df", lambda: prob.apply_factor(x64, 1, out=y64, dfloat=True))):
         fn()
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)

@@ -20,8 +20,8 @@
  *    lexicographic ordering of Section 2), interior points only, times
  *    t_1..t_nt (t = 0 is the zero initial state).
  *  - Unless stated otherwise, array arguments are DEVICE pointers owned by
- *    the caller, contiguous, of element type double (FDE_FP64 / FDE_MIXED) or
- *    float (FDE_FP32). They must stay valid until the work queued on `stream`
+ *    the caller, contiguous, of element type double (FDE_FP64 / FDE_MIXED /
+ *    FDE_MIXED_DF) or float (FDE_FP32). They must stay valid until the work queued on `stream`
  *    has finished.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream). All GPU work is queued on it; calls return when the work is
@@ -56,8 +56,21 @@ enum fde_status {
 enum fde_precision {
   FDE_FP64 = 0,   /* everything in double                                                   */
   FDE_FP32 = 1,   /* operator/preconditioner in float, float arrays (fde_matvec/fde_precond) */
-  FDE_MIXED = 2   /* solves only: float operator+preconditioner inside a double-precision
+  FDE_MIXED = 2,  /* solves only: float operator+preconditioner inside a double-precision
                      iterative-refinement loop; double arrays at the interface               */
+  FDE_MIXED_DF = 3, /* as FDE_MIXED, but the double products of the refinement (residuals,
+                     B y) run their FFTs in double-float arithmetic (a pair of floats,
+                     about 48 significand bits, relative error ~1e-14) instead of double;
+                     vectors, scalars and epilogues stay double. In fde_matvec: B or B^T
+                     (not S) on double arrays with that arithmetic. Not in the paper:
+                     a GB300 choice, its float rate is 58x its double rate               */
+  FDE_MIXED_DFV = 4 /* solves only: as FDE_MIXED_DF for the refinement evaluations that
+                     cannot be the last one (the next float correction cannot reach the
+                     target: rel * inner_tol_mixed > tol), double for the others; an
+                     evaluation that meets the target in double-float is repeated in
+                     double. The accepted residual of every sub-problem and the B y that
+                     feeds the ADMM step are double products. Batches: every evaluation
+                     but the last in double-float, the last in double.                  */
 };
 
 enum fde_op {
@@ -89,9 +102,30 @@ typedef struct fde_admm_opts {
   int max_pcg;               /* PCG iteration cap per sub-problem (per refinement step in MIXED)  */
   int inner_tol_mode;        /* 0: Section 6.1 rule 0.05 max{min residuals, tol_admm}; 1: fixed   */
   double inner_tol;          /* relative residual target of each sub-solve when inner_tol_mode=1  */
-  int precision;             /* FDE_FP64 or FDE_MIXED                                            */
+  int precision;             /* FDE_FP64, FDE_MIXED or FDE_MIXED_DF                              */
   double inner_tol_mixed;    /* MIXED: relative residual target of the float PCG per refinement   */
   int max_refine;            /* MIXED: cap on refinement steps per sub-problem                    */
+  int algorithm;             /* 0 or 1: Algorithm 1. 2: generalized ADMM (Section 3.3.2,
+                                Algorithm 2) with the proximal matrices R_y = c_y I - J1 and
+                                R_u = c_u I - J2 (1/2 on both proximal terms); it needs rho in
+                                (0, 1], c_y >= 1 (the largest weight of J1) and c_u >= gamma
+                                (of J2). Its M1, Q and M2 are multiples of the identity and the
+                                preconditioner uses them exactly.                                  */
+  double c_y, c_u;           /* Algorithm 2 only                                                  */
+  int inner_solver;          /* 0: PCG on the normal equations S y = rhs (Section 3.1) with
+                                S-tilde. 1: MINRES on the saddle-point system of y, u, p (Eq.
+                                generic ADMM subproblems 1and3 optimality conditions, Section
+                                3.3.1) with K-tilde = blkdiag(M1, Q, Sigma-tilde), Sigma-tilde =
+                                m2 I + C3 C3^T / m1. FP64 stops on the K-tilde^-1-norm of the
+                                residual, MIXED on its 2-norm (double residuals, float MINRES);
+                                max_pcg caps the MINRES iterations. Allocates 30N doubles (and
+                                30N floats in MIXED) on first use. fde_admm_solve only.             */
+  int precond;               /* PCG preconditioner (also fde_precond). 0: S-tilde (Eq. first schur
+                                complement preconditioner) with C3 and scalar m1, m2. 1: the
+                                matching approximation S-hat (Eq. second schur complement
+                                preconditioner, Section 3.2.2) with D-tilde = C3: D-hat = C3^T +
+                                sqrt(m1 m2) I is circulant, so S-hat is applied by the same FFTs
+                                with sigma = m1 + |Lambda|^2/m2 + 2 sqrt(m1/m2) Re(Lambda).         */
 } fde_admm_opts;
 
 typedef struct fde_admm_stats {
@@ -130,17 +164,17 @@ double fde_psi(const fde_problem* prob);
  * FDE_OP_S adds the normal-equation diagonals of Eq. (generic ADMM normal
  * equations) for the given ADMM options). Toeplitz products run by circulant
  * embedding and FFT (Table "Complexity table", d-level Toeplitz row).
- * precision: FDE_FP64 (x, y double*) or FDE_FP32 (float*). `opts` is read
- * only for FDE_OP_S (delta, rho) and may be NULL otherwise. x and y must not
- * overlap. Errors: FDE_EINVAL. */
+ * precision: FDE_FP64 (x, y double*), FDE_FP32 (float*) or FDE_MIXED_DF
+ * (double*, ops B and B^T only). `opts` is read only for FDE_OP_S (delta,
+ * rho) and may be NULL otherwise. x and y must not overlap. Errors: FDE_EINVAL. */
 int fde_matvec(fde_problem* prob, int op, const fde_admm_opts* opts, int precision,
                const void* x, void* y, void* stream);
 
 /* One Kronecker factor of B alone, one kernel launch: axis 1: y = -psi (I (x) X (x) I) x,
  * axis 2: y = -psi (I (x) I (x) Y) x, with X = d+ L_x + d- L_x^T and Y = e+ L_y + e- L_y^T
  * (Eq. FDE constraint matrix); op FDE_OP_BT applies the transposed factor. No
- * time term. precision FDE_FP64 (double*) or FDE_FP32 (float*); x and y must
- * not overlap. Errors: FDE_EINVAL. */
+ * time term. precision FDE_FP64 (double*), FDE_FP32 (float*) or FDE_MIXED_DF
+ * (double*, double-float transforms); x and y must not overlap. Errors: FDE_EINVAL. */
 int fde_apply_factor(fde_problem* prob, int axis, int op, int precision, const void* x, void* y, void* stream);
 
 /* FFT tile autotuning: times the float transform passes of this problem with
@@ -156,8 +190,11 @@ int fde_tiles(const fde_problem* prob, int* rows_threads, int* axis_threads);
 /* Preconditioner z = S~^-1 r with S~ = m1 I + C_3(B)^T C_3(B) / m2 (Eq. first
  * schur complement preconditioner with C_3 of Eq. multilevel circulant
  * preconditioner, J replaced by I): FFT, divide by m1 + |Lambda|^2/m2,
- * inverse FFT. precision: FDE_FP64 (double*) or FDE_FP32 (float*). r and z
- * may be the same array. Errors: FDE_EINVAL. */
+ * inverse FFT; with opts->precond = 1 the matching approximation S^ (divide by
+ * m1 + |Lambda|^2/m2 + 2 sqrt(m1/m2) Re Lambda). m1, m2 follow opts (Algorithm 2:
+ * exact scalars). precision: FDE_FP64 (double*) or FDE_FP32 (float*). r and z
+ * may be the same array. Errors: FDE_EINVAL, FDE_EUNSUPPORTED (an axis length
+ * with a prime factor above 7). */
 int fde_precond(fde_problem* prob, const fde_admm_opts* opts, int precision,
                 const void* r, void* z, void* stream);
 
@@ -242,7 +279,8 @@ long long fde_batch_instance_size(const fde_batch* batch, int i);
  * (device, N_i doubles); stats (HOST array of `count`, may be NULL;
  * max_sub_relres is the largest final relative residual over the
  * sub-problems). Synchronises `stream`. Errors: FDE_EINVAL (opts->precision
- * not FDE_MIXED, NULL pointers, NaN bounds), FDE_ENONFINITE, FDE_ECUDA. */
+ * not FDE_MIXED or FDE_MIXED_DF, NULL pointers, NaN bounds), FDE_ENONFINITE,
+ * FDE_ECUDA. */
 int fde_batch_admm_solve(fde_batch* batch, const fde_admm_opts* opts, const double* const* ybar,
                          const double* ya, const double* yb, const double* ua, const double* ub,
                          double* const* y, double* const* u, fde_admm_stats* stats, void* stream);

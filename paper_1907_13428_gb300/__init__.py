@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libfde.so")
 
 FDE_OK, FDE_EINVAL, FDE_ENOMEM, FDE_ECUDA, FDE_ENOCONV = 0, -1, -2, -3, -4
 FDE_EBREAKDOWN, FDE_ENONFINITE, FDE_EUNSUPPORTED = -5, -6, -8
-FDE_FP64, FDE_FP32, FDE_MIXED = 0, 1, 2
+FDE_FP64, FDE_FP32, FDE_MIXED, FDE_MIXED_DF, FDE_MIXED_DFV = 0, 1, 2, 3, 4
 FDE_OP_B, FDE_OP_BT, FDE_OP_S = 0, 1, 2
 
 
@@ -35,7 +35,9 @@ class fde_admm_opts(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("rho", ctypes.c_double), ("tol_admm", ctypes.c_double),
                 ("max_admm", ctypes.c_int), ("fixed_iters", ctypes.c_int), ("max_pcg", ctypes.c_int),
                 ("inner_tol_mode", ctypes.c_int), ("inner_tol", ctypes.c_double), ("precision", ctypes.c_int),
-                ("inner_tol_mixed", ctypes.c_double), ("max_refine", ctypes.c_int)]
+                ("inner_tol_mixed", ctypes.c_double), ("max_refine", ctypes.c_int), ("algorithm", ctypes.c_int),
+                ("c_y", ctypes.c_double), ("c_u", ctypes.c_double), ("inner_solver", ctypes.c_int),
+                ("precond", ctypes.c_int)]
 
 
 class fde_admm_stats(ctypes.Structure):
@@ -149,11 +151,16 @@ class AdmmOptions:
     precision: int = FDE_FP64
     inner_tol_mixed: float = 1e-4
     max_refine: int = 30
+    algorithm: int = 1             # 2: generalized ADMM (Algorithm 2), rho in (0, 1]
+    c_y: float = 0.0               # Algorithm 2: R_y = c_y I - J1, c_y >= 1
+    c_u: float = 0.0               # Algorithm 2: R_u = c_u I - J2, c_u >= gamma
+    inner_solver: int = 0          # 0: PCG on the normal equations, 1: MINRES on the saddle-point system
+    precond: int = 0               # 0: S-tilde, 1: matching approximation S-hat (circulant D-tilde)
 
     def c(self) -> fde_admm_opts:
         return fde_admm_opts(self.delta, self.rho, self.tol_admm, self.max_admm, int(self.fixed_iters), self.max_pcg,
                              self.inner_tol_mode, self.inner_tol, self.precision, self.inner_tol_mixed,
-                             self.max_refine)
+                             self.max_refine, self.algorithm, self.c_y, self.c_u, self.inner_solver, self.precond)
 
 
 def params_struct(p) -> fde_params:
@@ -191,8 +198,14 @@ class Problem:
         return self._h
 
     def matvec(self, x: torch.Tensor, op: int = FDE_OP_B, opts: Optional[AdmmOptions] = None,
-               out: Optional[torch.Tensor] = None) -> torch.Tensor:
+               out: Optional[torch.Tensor] = None, dfloat: bool = False) -> torch.Tensor:
+        """y = op(x); float64 or float32 x. dfloat: float64 B / B^T with the
+        transforms in double-float arithmetic (FDE_MIXED_DF)."""
         prec = FDE_FP64 if x.dtype == torch.float64 else FDE_FP32
+        if dfloat:
+            if x.dtype != torch.float64:
+                raise ValueError("dfloat products take float64 vectors")
+            prec = FDE_MIXED_DF
         y = torch.empty_like(x) if out is None else out
         o = (opts or AdmmOptions()).c()
         _check(lib().fde_matvec(self._h, op, ctypes.byref(o), prec, _ptr(x, None, self.N), _ptr(y, x.dtype, self.N),
@@ -209,9 +222,15 @@ class Problem:
         _check(lib().fde_tiles(self._h, ctypes.byref(a), ctypes.byref(c)), "fde_tiles")
         return a.value, c.value
 
-    def apply_factor(self, x: torch.Tensor, axis: int, op: int = FDE_OP_B, out=None) -> torch.Tensor:
-        """One Kronecker factor of B along x1 (axis 1) or x2 (axis 2): one kernel launch."""
+    def apply_factor(self, x: torch.Tensor, axis: int, op: int = FDE_OP_B, out=None,
+                     dfloat: bool = False) -> torch.Tensor:
+        """One Kronecker factor of B along x1 (axis 1) or x2 (axis 2): one kernel
+        launch. dfloat: float64 vectors, double-float transform arithmetic."""
         prec = FDE_FP64 if x.dtype == torch.float64 else FDE_FP32
+        if dfloat:
+            if x.dtype != torch.float64:
+                raise ValueError("dfloat products take float64 vectors")
+            prec = FDE_MIXED_DF
         y = torch.empty_like(x) if out is None else out
         _check(lib().fde_apply_factor(self._h, axis, op, prec, _ptr(x, None, self.N), _ptr(y, x.dtype, self.N),
                                       _stream()), "fde_apply_factor")

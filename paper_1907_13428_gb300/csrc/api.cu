@@ -9,6 +9,7 @@
 #include <cstring>
 
 #include "internal.h"
+#include "saddle.h"
 #include "vec.h"
 
 using namespace fde;
@@ -57,21 +58,37 @@ namespace {
 struct Diags {
   SliceDiag w, M1, Q, M2, M2inv;
   double m1, m2;  // preconditioner scalars (J ~ I)
+  double cre;     // matching approximation S^: 2 sqrt(m1/m2) (coefficient of Re Lambda), else 0
 };
 
-Diags make_diags(const fde_problem* P, double delta, double rho) {
+bool generalized(const fde_admm_opts* o) { return o->algorithm == 2; }
+
+// Algorithm 1: M1 = rho (J1 + I/delta), Q = rho (J2 + psi^2/delta), M2 = psi^2/Q + delta/rho,
+// preconditioner scalars with J ~ I. Algorithm 2: J1 + R_y = c_y I and J2 + R_u = c_u I, so
+// all three are scalars and the preconditioner takes them as they are.
+Diags make_diags(const fde_problem* P, const fde_admm_opts* o) {
   Diags d{};
+  const double delta = o->delta, rho = o->rho;
   const double psi2 = P->psi * P->psi;
   d.w.v[0] = 1.0;
   d.w.v[1] = P->prm.weights == 0 ? 0.5 : 1.0;
+  const bool gen = generalized(o);
   for (int s = 0; s < 2; ++s) {
-    d.M1.v[s] = rho * (d.w.v[s] + 1.0 / delta);
-    d.Q.v[s] = rho * (P->prm.gamma * d.w.v[s] + psi2 / delta);
+    d.M1.v[s] = gen ? rho * (o->c_y + 1.0 / delta) : rho * (d.w.v[s] + 1.0 / delta);
+    d.Q.v[s] = gen ? rho * (o->c_u + psi2 / delta) : rho * (P->prm.gamma * d.w.v[s] + psi2 / delta);
     d.M2.v[s] = psi2 / d.Q.v[s] + delta / rho;
     d.M2inv.v[s] = 1.0 / d.M2.v[s];
   }
-  d.m1 = rho * (1.0 + 1.0 / delta);
-  d.m2 = psi2 / (rho * (P->prm.gamma + psi2 / delta)) + delta / rho;
+  if (gen) {
+    d.m1 = d.M1.v[0];
+    d.m2 = d.M2.v[0];
+  } else {
+    d.m1 = rho * (1.0 + 1.0 / delta);
+    d.m2 = psi2 / (rho * (P->prm.gamma + psi2 / delta)) + delta / rho;
+  }
+  // matching Schur approximation with D~ = C3(B): D^ = C3^T + sqrt(m1 m2) I is circulant and
+  // S^ = D^ D^T / m2 has the eigenvalues m1 + |Lambda|^2/m2 + 2 sqrt(m1/m2) Re(Lambda)
+  d.cre = o->precond == 1 ? 2.0 * std::sqrt(d.m1 / d.m2) : 0.0;
   return d;
 }
 
@@ -111,13 +128,41 @@ AdmmArgs make_admm_args(fde_problem* P, const fde_admm_opts* o, const Diags& dg,
   A.p = P->v64[V_P];
   A.wy = P->v64[V_WY];
   A.wu = P->v64[V_WU];
+  if (generalized(o)) {
+    A.gen = 1;
+    for (int s = 0; s < 2; ++s) {
+      A.ry[s] = o->rho * (o->c_y - dg.w.v[s]);
+      A.ru[s] = o->rho * (o->c_u - P->prm.gamma * dg.w.v[s]);
+    }
+    A.yprev = P->v64[V_Y];  // y^j and u^j: the iterates before this iteration's update
+    A.uprev = P->v64[V_U];
+  }
   return A;
 }
 
 bool valid_opts(const fde_admm_opts* o) {
   if (!o) return false;
   const double golden = (1.0 + std::sqrt(5.0)) / 2.0;
-  return std::isfinite(o->delta) && o->delta > 0 && std::isfinite(o->rho) && o->rho > 0 && o->rho < golden;
+  if (!(std::isfinite(o->delta) && o->delta > 0 && std::isfinite(o->rho) && o->rho > 0 && o->rho < golden))
+    return false;
+  if (o->algorithm < 0 || o->algorithm > 2) return false;
+  if (o->inner_solver < 0 || o->inner_solver > 1) return false;
+  if (o->precond < 0 || o->precond > 1) return false;
+  if (generalized(o)) return o->rho <= 1.0 && std::isfinite(o->c_y) && o->c_y >= 1.0 && std::isfinite(o->c_u);
+  return true;
+}
+
+// Problem-dependent part of the option check: R_u = c_u I - J2 must be positive semi-definite.
+bool valid_opts_for(const fde_problem* P, const fde_admm_opts* o) {
+  return valid_opts(o) && (!generalized(o) || o->c_u >= P->prm.gamma);
+}
+
+// Double product of the mixed refinement: B or B^T on double vectors, with
+// double (dd = false) or double-float (dd = true) transform arithmetic.
+cudaError_t refine_B(fde_problem* P, bool dd, int transpose, const double* x, double* y, const double* addv,
+                     const SliceDiag* addc, double* t1, double* t2, cudaStream_t st, Gate gate = {}) {
+  if (dd) return apply_B_df(P, transpose, x, y, nullptr, addv, addc, t1, t2, st, gate);
+  return apply_B<double>(P, transpose, x, y, nullptr, addv, addc, t1, t2, st, gate);
 }
 
 int read_scalars(fde_problem* P, cudaStream_t st) {
@@ -208,7 +253,7 @@ int op_S(fde_problem* P, const Diags& dg, const R* x, R* y, Scratch<R> s, cudaSt
 }
 template <typename R>
 int op_M(fde_problem* P, const Diags& dg, const R* r, R* z, cudaStream_t st, Gate gate = {}) {
-  CK(apply_precond<R>(P, dg.m1, dg.m2, 0, r, z, spec<R>(P), st, gate));
+  CK(apply_precond<R>(P, dg.m1, dg.m2, 0, r, z, spec<R>(P), st, gate, dg.cre));
   return FDE_OK;
 }
 
@@ -261,23 +306,38 @@ int subsolve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const doub
   const int maxref = o->max_refine > 0 ? o->max_refine : 20;
   auto A32 = [&](const float* x, float* out) { return op_S<float>(P, dg, x, out, s32, st); };
   auto M32 = [&](const float* r, float* z) { return op_M<float>(P, dg, r, z, st); };
+  // FDE_MIXED_DFV: an evaluation that cannot be the last one (the next correction cannot
+  // reach tol: rel * inner > tol) runs its products in double-float; the others, and a
+  // re-check of any double-float evaluation that meets tol, in double, so that the
+  // accepted residual and B y are double products.
+  const bool dfv = o->precision == FDE_MIXED_DFV;
+  bool dd = o->precision == FDE_MIXED_DF || dfv;
+  bool by_dd = o->precision == FDE_MIXED_DF;  // V_BY holds a double-float product
   for (int k = 0; k <= maxref; ++k) {
+    double rel = 0.0;
     // on entry V_BY already holds B y for the warm start (kept by the ADMM loop)
-    if (k > 0 || !by_on_entry) {
-      CK(apply_B<double>(P, 0, y, P->v64[V_BY], nullptr, nullptr, nullptr, s64.t1, s64.t2, st));
+    const bool y_changed = k > 0 || !by_on_entry;
+    for (int pass = 0; pass < 2; ++pass) {
+      if ((pass == 0 && y_changed) || (by_dd && !dd)) {
+        CK(refine_B(P, dd, 0, y, P->v64[V_BY], nullptr, nullptr, s64.t1, s64.t2, st));
+        info->fp64_matvecs += 1;
+        by_dd = dd;
+      }
+      CK(fold(P->v64[V_BY], q, c, y, dg.M2inv.v, dg.M1.v, last, N, P->v64[V_SD], P->v64[V_Z], st));
+      CK(refine_B(P, dd, 1, P->v64[V_SD], P->v64[V_R], P->v64[V_Z], &one, s64.t1, s64.t2, st));
       info->fp64_matvecs += 1;
+      *by_valid = !by_dd || o->precision == FDE_MIXED_DF;
+      CK((dot<double, double>(P, P->v64[V_R], P->v64[V_R], N, S_RR, FIN_STORE, st)));
+      flag = read_scalars(P, st);
+      if (flag < 0) return flag;
+      rel = std::sqrt(P->hscal[S_RR] / bb);
+      if (!(dfv && dd && rel <= tol)) break;
+      dd = false;  // met tol in double-float: evaluate again in double
     }
-    CK(fold(P->v64[V_BY], q, c, y, dg.M2inv.v, dg.M1.v, last, N, P->v64[V_SD], P->v64[V_Z], st));
-    CK(apply_B<double>(P, 1, P->v64[V_SD], P->v64[V_R], nullptr, P->v64[V_Z], &one, s64.t1, s64.t2, st));
-    info->fp64_matvecs += 1;
-    *by_valid = true;
-    CK((dot<double, double>(P, P->v64[V_R], P->v64[V_R], N, S_RR, FIN_STORE, st)));
-    flag = read_scalars(P, st);
-    if (flag < 0) return flag;
-    const double rel = std::sqrt(P->hscal[S_RR] / bb);
     info->relres = rel;
     if (rel <= tol) return FDE_OK;
     if (k == maxref) break;
+    if (dfv) dd = rel * inner > tol;
     CK(to_f32(P->v64[V_R], P->v32[F_B], N, st));
     int it = 0;
     double rr32 = 0;
@@ -289,6 +349,224 @@ int subsolve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const doub
     if (s != FDE_OK && s != FDE_ENOCONV) return s;
     CK(add_f32(y, P->v32[F_X], N, st));
     *by_valid = false;
+  }
+  return FDE_ENOCONV;
+}
+
+// ---------------------------------------------------------------------------
+// Saddle-point sub-problem (Section 3.3.1): K [y; u; p] = [b_y; b_u; f_p] by
+// preconditioned MINRES with K-tilde = blkdiag(M1, Q, Sigma-tilde), where
+// Sigma-tilde = m2 I + C3 C3^T / m1 stands in for the p-block Schur complement
+// M2 + B M1^-1 B^T (the FFT-diagonal form of S-tilde with m1 and m2 exchanged).
+// A vector of this system is [y | u | p], 3N contiguous entries.
+// ---------------------------------------------------------------------------
+
+// Workspace of the saddle-point path, allocated on first use: 10 vectors of 3N
+// doubles (x, f, and MINRES's or the refinement's vectors) and, for the mixed
+// path, 10 of 3N floats.
+int saddle_workspace(fde_problem* P, bool need32) {
+  const size_t n3 = 3 * (size_t)P->N;
+  void* ptr = nullptr;
+  if (!P->mr64) {
+    CK(fde_alloc(P, &ptr, sizeof(double) * n3 * 10));
+    P->mr64 = (double*)ptr;
+  }
+  if (need32 && !P->mr32) {
+    CK(fde_alloc(P, &ptr, sizeof(float) * n3 * 10));
+    P->mr32 = (float*)ptr;
+  }
+  return FDE_OK;
+}
+
+// q = K z: q_y = M1 z_y + B^T z_p, q_u = Q z_u + psi z_p, q_p = B z_y + psi z_u - (delta/rho) z_p.
+// df: the double products in double-float arithmetic.
+template <typename R>
+int op_K(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const R* z, R* q, Scratch<R> s, cudaStream_t st,
+         bool df = false) {
+  const long long N = P->N, last = (long long)(P->nt - 1) * P->nx * P->ny;
+  const R *zy = z, *zu = z + N, *zp = z + 2 * N;
+  R *qy = q, *qu = q + N, *qp = q + 2 * N;
+  if constexpr (sizeof(R) == 8) {
+    if (df) {
+      CK(apply_B_df(P, 1, zp, qy, nullptr, zy, &dg.M1, s.t1, s.t2, st));
+      CK(apply_B_df(P, 0, zy, qp, nullptr, nullptr, nullptr, s.t1, s.t2, st));
+    } else {
+      CK(apply_B<R>(P, 1, zp, qy, nullptr, zy, &dg.M1, s.t1, s.t2, st));
+      CK(apply_B<R>(P, 0, zy, qp, nullptr, nullptr, nullptr, s.t1, s.t2, st));
+    }
+  } else {
+    CK(apply_B<R>(P, 1, zp, qy, nullptr, zy, &dg.M1, s.t1, s.t2, st));
+    CK(apply_B<R>(P, 0, zy, qp, nullptr, nullptr, nullptr, s.t1, s.t2, st));
+  }
+  CK(saddle_tail<R>(N, last, dg.Q.v, P->psi, o->delta / o->rho, zu, zp, qu, qp, st));
+  return FDE_OK;
+}
+
+// z = K-tilde^-1 r.
+template <typename R>
+int op_Kt(fde_problem* P, const Diags& dg, const R* r, R* z, cudaStream_t st) {
+  const long long N = P->N, last = (long long)(P->nt - 1) * P->nx * P->ny;
+  CK(block_diag<R>(N, last, dg.M1.v, dg.Q.v, r, z, st));
+  CK(apply_precond<R>(P, dg.m2, dg.m1, 0, r + 2 * N, z + 2 * N, spec<R>(P), st));
+  return FDE_OK;
+}
+
+// Preconditioned MINRES (Paige and Saunders) on a symmetric operator A with a
+// symmetric positive definite preconditioner M: the Lanczos process in the
+// M^-1 inner product; its tridiagonal is factored by Givens rotations on the
+// host from the two inner products of each iteration (read back together). x
+// minimises ||b - A x||_{M^-1} over the Krylov space; the rotations give that
+// norm, |eta|, and the solve stops when |eta| <= tol ||b||_{M^-1}. x holds the
+// initial guess unless x_zero. wk: 7 vectors of n.
+template <typename R, class OpA, class OpM>
+int minres(fde_problem* P, OpA A, OpM M, const R* b, R* x, bool x_zero, double tol, int maxit, R* const* wk,
+           long long n, cudaStream_t st, int* iters, double* relres) {
+  R *vp = wk[0], *v = wk[1], *z = wk[2], *zn = wk[3], *wp = wk[4], *w = wk[5], *q = wk[6];
+  *iters = 0;
+  RK(clear_flag(P, st));
+  RK(M(b, z));
+  CK((dot<R, R>(P, b, z, n, S_BB, FIN_STORE, st)));
+  if (x_zero) {
+    CK(fill<R>(x, (R)0, n, st));
+    CK(copy<R>(v, b, n, st));
+  } else {
+    RK(A(x, q));
+    CK(lin3<R>(n, 1.0, b, -1.0, nullptr, 0, q, 0.0, q, v, st));
+  }
+  RK(M(v, z));
+  CK((dot<R, R>(P, v, z, n, S_RR, FIN_STORE, st)));
+  int flag = read_scalars(P, st);
+  if (flag < 0) return flag;
+  const double bn = std::sqrt(std::fmax(P->hscal[S_BB], 0.0));
+  double beta = std::sqrt(std::fmax(P->hscal[S_RR], 0.0));
+  if (bn == 0.0) {
+    CK(fill<R>(x, (R)0, n, st));
+    *relres = 0.0;
+    return FDE_OK;
+  }
+  double eta = beta;
+  if (eta <= tol * bn) {
+    *relres = eta / bn;
+    return FDE_OK;
+  }
+  CK(fill<R>(vp, (R)0, n, st));
+  CK(fill<R>(wp, (R)0, n, st));
+  CK(fill<R>(w, (R)0, n, st));
+  double beta_prev = 1.0, c_prev = 1.0, c = 1.0, s_prev = 0.0, s = 0.0;
+  for (int it = 1; it <= maxit; ++it) {
+    // z holds the unnormalised M^-1 v_k; the Lanczos vector is z / beta
+    RK(A(z, q));
+    CK((dot<R, R>(P, q, z, n, S_TMP0, FIN_STORE, st)));  // alpha beta^2
+    // v_{k+1} = q / beta - (alpha / beta) v_k - (beta / beta_prev) v_{k-1}, into v_{k-1}'s storage
+    CK(lin3<R>(n, 1.0 / beta, q, -1.0 / (beta * beta * beta), P->dscal, S_TMP0, v, -beta / beta_prev, vp, vp, st));
+    RK(M(vp, zn));
+    CK((dot<R, R>(P, vp, zn, n, S_TMP1, FIN_STORE, st)));
+    flag = read_scalars(P, st);
+    if (flag < 0) return flag;
+    const double alpha = P->hscal[S_TMP0] / (beta * beta);
+    const double beta_next = std::sqrt(std::fmax(P->hscal[S_TMP1], 0.0));
+    // column k of the tridiagonal after the rotations k-2 and k-1, then the new rotation
+    const double e3 = s_prev * beta;
+    const double e2 = s * alpha + c_prev * c * beta;
+    const double e0 = c * alpha - c_prev * s * beta;
+    const double e1 = std::hypot(e0, beta_next);
+    if (!(e1 > 0.0) || !std::isfinite(e1)) return FDE_EBREAKDOWN;
+    const double c_new = e0 / e1, s_new = beta_next / e1;
+    // w_{k+1} = (z / beta - e3 w_{k-1} - e2 w_k) / e1 into w_{k-1}'s storage; x += c_new eta w_{k+1}
+    CK(minres_wx<R>(n, 1.0 / (beta * e1), z, -e3 / e1, wp, -e2 / e1, w, c_new * eta, x, st));
+    eta = -s_new * eta;
+    *iters = it;
+    if (std::fabs(eta) <= tol * bn) {
+      *relres = std::fabs(eta) / bn;
+      return FDE_OK;
+    }
+    std::swap(vp, v);
+    std::swap(wp, w);
+    std::swap(z, zn);
+    beta_prev = beta;
+    beta = beta_next;
+    c_prev = c;
+    c = c_new;
+    s_prev = s;
+    s = s_new;
+    if (beta == 0.0) {  // invariant Krylov space: x is exact
+      *relres = std::fabs(eta) / bn;
+      return FDE_OK;
+    }
+  }
+  *relres = std::fabs(eta) / bn;
+  return FDE_ENOCONV;
+}
+
+// Solve K x = f (3N, double), x holding a warm start. FP64: MINRES in double,
+// stopping on ||r||_{K-tilde^-1} <= tol ||f||_{K-tilde^-1}. MIXED / MIXED_DF:
+// double (or double-float) residuals r = f - K x, float MINRES on K d = r to
+// max(inner, tol / (2 rel)), x += d, until ||r||_2 <= tol ||f||_2.
+int saddle_solve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const double* f, double* x, double tol,
+                 cudaStream_t st, SolveInfo* info) {
+  const long long n3 = 3 * P->N;
+  double* wk64[7];
+  for (int i = 0; i < 7; ++i) wk64[i] = P->mr64 + (size_t)(3 + i) * n3;
+  auto s64 = scratch64(P);
+  if (o->precision == FDE_FP64) {
+    auto A = [&](const double* z, double* q) { return op_K<double>(P, dg, o, z, q, s64, st); };
+    auto M = [&](const double* r, double* z) { return op_Kt<double>(P, dg, r, z, st); };
+    int it = 0;
+    double rel = 0.0;
+    const int s = minres<double>(P, A, M, f, x, false, tol, o->max_pcg, wk64, n3, st, &it, &rel);
+    info->pcg_iters += it;
+    info->fp64_matvecs += 2 * (it + 1);
+    info->relres = rel;
+    return s;
+  }
+  const bool dfv = o->precision == FDE_MIXED_DFV;
+  bool dd = o->precision == FDE_MIXED_DF || dfv;
+  double* r64 = P->mr64 + 2 * (size_t)n3;
+  float* b32 = P->mr32;
+  float* d32 = P->mr32 + n3;
+  float* wk32[7];
+  for (int i = 0; i < 7; ++i) wk32[i] = P->mr32 + (size_t)(2 + i) * n3;
+  auto s32 = scratch32(P);
+  auto A32 = [&](const float* z, float* q) { return op_K<float>(P, dg, o, z, q, s32, st); };
+  auto M32 = [&](const float* r, float* z) { return op_Kt<float>(P, dg, r, z, st); };
+  RK(clear_flag(P, st));
+  CK((dot<double, double>(P, f, f, n3, S_BB, FIN_STORE, st)));
+  int flag = read_scalars(P, st);
+  if (flag < 0) return flag;
+  const double ff = P->hscal[S_BB];  // read once: the float MINRES reuses the slot
+  const double inner = o->inner_tol_mixed > 0 ? o->inner_tol_mixed : 1e-4;
+  const int maxref = o->max_refine > 0 ? o->max_refine : 20;
+  if (ff == 0.0) {
+    CK(fill<double>(x, 0.0, n3, st));
+    info->relres = 0.0;
+    return FDE_OK;
+  }
+  for (int k = 0; k <= maxref; ++k) {
+    double rel = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {  // as in subsolve: a double re-check of a double-float pass
+      RK(op_K<double>(P, dg, o, x, r64, s64, st, dd));
+      info->fp64_matvecs += 2;
+      CK(lin3<double>(n3, 1.0, f, -1.0, nullptr, 0, r64, 0.0, r64, r64, st));
+      CK((dot<double, double>(P, r64, r64, n3, S_RR, FIN_STORE, st)));
+      flag = read_scalars(P, st);
+      if (flag < 0) return flag;
+      rel = std::sqrt(P->hscal[S_RR] / ff);
+      if (!(dfv && dd && rel <= tol)) break;
+      dd = false;
+    }
+    info->relres = rel;
+    if (rel <= tol) return FDE_OK;
+    if (k == maxref) break;
+    if (dfv) dd = rel * inner > tol;
+    CK(to_f32(r64, b32, n3, st));
+    int it = 0;
+    double rr = 0.0;
+    const int s = minres<float>(P, A32, M32, b32, d32, true, std::fmax(inner, 0.5 * tol / rel), o->max_pcg, wk32, n3,
+                                st, &it, &rr);
+    info->pcg_iters += it;
+    info->refine += 1;
+    if (s != FDE_OK && s != FDE_ENOCONV) return s;
+    CK(add_f32(x, d32, n3, st));
   }
   return FDE_ENOCONV;
 }
@@ -403,20 +681,24 @@ int fde_setup(const fde_params* prm, fde_problem** out, void* stream) {
 int fde_matvec(fde_problem* P, int op, const fde_admm_opts* o, int precision, const void* x, void* y, void* stream) {
   if (!P || !x || !y || x == y) return FDE_EINVAL;
   if (op != FDE_OP_B && op != FDE_OP_BT && op != FDE_OP_S) return FDE_EINVAL;
-  if (precision != FDE_FP64 && precision != FDE_FP32) return FDE_EINVAL;
-  if (op == FDE_OP_S && !valid_opts(o)) return FDE_EINVAL;
+  if (precision != FDE_FP64 && precision != FDE_FP32 && precision != FDE_MIXED_DF) return FDE_EINVAL;
+  if (op == FDE_OP_S && !valid_opts_for(P, o)) return FDE_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  if (precision == FDE_FP64) {
+  if (precision == FDE_MIXED_DF) {
+    if (op == FDE_OP_S) return FDE_EINVAL;
+    auto s = scratch64(P);
+    CK(apply_B_df(P, op == FDE_OP_BT, (const double*)x, (double*)y, nullptr, nullptr, nullptr, s.t1, s.t2, st));
+  } else if (precision == FDE_FP64) {
     auto s = scratch64(P);
     if (op == FDE_OP_S) {
-      const Diags dg = make_diags(P, o->delta, o->rho);
+      const Diags dg = make_diags(P, o);
       return op_S<double>(P, dg, (const double*)x, (double*)y, s, st);
     }
     CK(apply_B<double>(P, op == FDE_OP_BT, (const double*)x, (double*)y, nullptr, nullptr, nullptr, s.t1, s.t2, st));
   } else {
     auto s = scratch32(P);
     if (op == FDE_OP_S) {
-      const Diags dg = make_diags(P, o->delta, o->rho);
+      const Diags dg = make_diags(P, o);
       return op_S<float>(P, dg, (const float*)x, (float*)y, s, st);
     }
     CK(apply_B<float>(P, op == FDE_OP_BT, (const float*)x, (float*)y, nullptr, nullptr, nullptr, s.t1, s.t2, st));
@@ -445,6 +727,8 @@ int fde_apply_factor(fde_problem* P, int axis, int op, int precision, const void
     CK(apply_axis_raw<double>(P, axis, (const double*)x, (double*)y, P->ax[axis].d.sym, conj, st));
   } else if (precision == FDE_FP32) {
     CK(apply_axis_raw<float>(P, axis, (const float*)x, (float*)y, P->ax[axis].f.sym, conj, st));
+  } else if (precision == FDE_MIXED_DF) {
+    CK(apply_axis_raw_df(P, axis, (const double*)x, (double*)y, conj, st));
   } else {
     return FDE_EINVAL;
   }
@@ -452,12 +736,12 @@ int fde_apply_factor(fde_problem* P, int axis, int op, int precision, const void
 }
 
 int fde_precond(fde_problem* P, const fde_admm_opts* o, int precision, const void* r, void* z, void* stream) {
-  if (!P || !r || !z || !valid_opts(o)) return FDE_EINVAL;
+  if (!P || !r || !z || !valid_opts_for(P, o)) return FDE_EINVAL;
   if (precision != FDE_FP64 && precision != FDE_FP32) return FDE_EINVAL;
   for (int a = 0; a < 3; ++a)
     if (!P->ax[a].n_ok) return FDE_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
-  const Diags dg = make_diags(P, o->delta, o->rho);
+  const Diags dg = make_diags(P, o);
   if (precision == FDE_FP64) return op_M<double>(P, dg, (const double*)r, (double*)z, st);
   return op_M<float>(P, dg, (const float*)r, (float*)z, st);
 }
@@ -465,15 +749,17 @@ int fde_precond(fde_problem* P, const fde_admm_opts* o, int precision, const voi
 int fde_admm_solve(fde_problem* P, const fde_admm_opts* o, const double* ybar, const double* g, const double* ya,
                    const double* yb, const double* ua, const double* ub, double ya_s, double yb_s, double ua_s,
                    double ub_s, double* y, double* u, double* p, double* zu, fde_admm_stats* stats, void* stream) {
-  if (!P || !valid_opts(o) || !ybar || !y || !u) return FDE_EINVAL;
-  if (o->precision != FDE_FP64 && o->precision != FDE_MIXED) return FDE_EINVAL;
+  if (!P || !valid_opts_for(P, o) || !ybar || !y || !u) return FDE_EINVAL;
+  if (o->precision != FDE_FP64 && o->precision != FDE_MIXED && o->precision != FDE_MIXED_DF &&
+      o->precision != FDE_MIXED_DFV)
+    return FDE_EINVAL;
   if (o->max_admm < 1 || o->max_pcg < 1) return FDE_EINVAL;
   if (std::isnan(ya_s) || std::isnan(yb_s) || std::isnan(ua_s) || std::isnan(ub_s)) return FDE_EINVAL;
   for (int a = 0; a < 3; ++a)
     if (!P->ax[a].n_ok) return FDE_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   const long long N = P->N;
-  const Diags dg = make_diags(P, o->delta, o->rho);
+  const Diags dg = make_diags(P, o);
 
   AdmmArgs A = make_admm_args(P, o, dg, ybar, g, ya, yb, ua, ub, ya_s, yb_s, ua_s, ub_s);
   double* Y = P->v64[V_Y];
@@ -487,19 +773,52 @@ int fde_admm_solve(fde_problem* P, const fde_admm_opts* o, const double* ybar, c
   int status = FDE_ENOCONV;
   auto s64 = scratch64(P);
   const SliceDiag one{{1.0, 1.0}};
+  const bool saddle = o->inner_solver == 1;
+  if (saddle) RK(saddle_workspace(P, o->precision != FDE_FP64));
+  AdmmArgs Ag = A;  // post-step taking u and p from the saddle-point solve
+  Ag.given_up = 1;
   for (int j = 0; j < o->max_admm; ++j) {
     CK(admm_pre(A, P->v64[V_C], P->v64[V_BU], P->v64[V_R0], P->v64[V_Q], st));
-    if (o->precision == FDE_FP64) {
-      // rhs = c + B^T q
-      CK(apply_B<double>(P, 1, P->v64[V_Q], P->v64[V_RHS], nullptr, P->v64[V_C], &one, s64.t1, s64.t2, st));
-      info.fp64_matvecs += 1;
-    }
     double tol;
     if (o->inner_tol_mode == 1) {
       tol = o->inner_tol;
     } else {
       const double mn = std::fmin(res[0], std::fmin(res[1], res[2]));
       tol = 0.05 * std::fmax(mn, o->tol_admm);
+    }
+    if (saddle) {
+      const size_t n3 = 3 * (size_t)N;
+      double* X = P->mr64;
+      double* F = P->mr64 + n3;
+      // f_y = c + (1 - rho) B^T p^j, f_u = b_u, f_p = psi g - (delta/rho) p^j
+      const SliceDiag omr{{1.0 - o->rho, 1.0 - o->rho}};
+      if (o->precision == FDE_MIXED_DF)
+        CK(apply_B_df(P, 1, A.p, F, &omr, P->v64[V_C], &one, s64.t1, s64.t2, st));
+      else
+        CK(apply_B<double>(P, 1, A.p, F, &omr, P->v64[V_C], &one, s64.t1, s64.t2, st));
+      CK(saddle_rhs(N, P->psi, o->delta / o->rho, P->v64[V_BU], g, A.p, F + N, F + 2 * N, st));
+      // warm start from (y^j, u^j, p^j)
+      CK(cudaMemcpyAsync(X, Y, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(X + N, U, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(X + 2 * N, A.p, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+      const int s = saddle_solve(P, dg, o, F, X, tol, st, &info);
+      if (s != FDE_OK && s != FDE_ENOCONV) {
+        status = s;
+        break;
+      }
+      S.max_sub_relres = std::fmax(S.max_sub_relres, info.relres);
+      CK(cudaMemcpyAsync(Y, X, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(U, X + N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(A.p, X + 2 * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+      CK(refine_B(P, o->precision == FDE_MIXED_DF, 0, Y, P->v64[V_BY], nullptr, nullptr, s64.t1, s64.t2, st));
+      info.fp64_matvecs += 1;
+      RK(clear_flag(P, st));
+      CK(admm_post(P, Ag, Y, P->v64[V_BY], P->v64[V_BU], P->v64[V_R0], U, st));
+    } else {
+    if (o->precision == FDE_FP64) {
+      // rhs = c + B^T q
+      CK(apply_B<double>(P, 1, P->v64[V_Q], P->v64[V_RHS], nullptr, P->v64[V_C], &one, s64.t1, s64.t2, st));
+      info.fp64_matvecs += 1;
     }
     bool by_valid = false;
     const int s = subsolve(P, dg, o, P->v64[V_RHS], P->v64[V_C], P->v64[V_Q], Y, tol, st, &info, true, &by_valid);
@@ -509,11 +828,12 @@ int fde_admm_solve(fde_problem* P, const fde_admm_opts* o, const double* ybar, c
     }
     S.max_sub_relres = std::fmax(S.max_sub_relres, info.relres);
     if (!by_valid) {
-      CK(apply_B<double>(P, 0, Y, P->v64[V_BY], nullptr, nullptr, nullptr, s64.t1, s64.t2, st));
+      CK(refine_B(P, o->precision == FDE_MIXED_DF, 0, Y, P->v64[V_BY], nullptr, nullptr, s64.t1, s64.t2, st));
       info.fp64_matvecs += 1;
     }
     RK(clear_flag(P, st));
     CK(admm_post(P, A, Y, P->v64[V_BY], P->v64[V_BU], P->v64[V_R0], U, st));
+    }
     const int flag = read_scalars(P, st);
     S.admm_iters = j + 1;
     res[0] = P->hscal[S_RES_EQ];
@@ -640,7 +960,7 @@ int pcg_fixed(fde_problem* P, OpA A, OpM M, const R* b, R* x, double tol, int it
 int enqueue_admm_fixed(fde_problem* P, const fde_admm_opts* o, const double* ybar, double ya_s, double yb_s,
                        double ua_s, double ub_s, double* y, double* u, cudaStream_t st) {
   const long long N = P->N;
-  const Diags dg = make_diags(P, o->delta, o->rho);
+  const Diags dg = make_diags(P, o);
   AdmmArgs A = make_admm_args(P, o, dg, ybar, nullptr, nullptr, nullptr, nullptr, nullptr, ya_s, yb_s, ua_s, ub_s);
   double* Y = P->v64[V_Y];
   double* U = P->v64[V_U];
@@ -658,6 +978,7 @@ int enqueue_admm_fixed(fde_problem* P, const fde_admm_opts* o, const double* yba
   const double tol = o->inner_tol > 0 ? o->inner_tol : 1e-8;
   const double inner = o->inner_tol_mixed > 0 ? o->inner_tol_mixed : 1e-4;
   const int evals = (o->max_refine > 0 ? o->max_refine : 2) + 1;
+  const bool dfv = o->precision == FDE_MIXED_DFV;
   for (int j = 0; j < o->max_admm; ++j) {
     CK(admm_pre(A, P->v64[V_C], P->v64[V_BU], P->v64[V_R0], P->v64[V_Q], st));
     // ||rhs||^2 of rhs = c + B^T q, in float (only the stopping test uses it)
@@ -666,12 +987,16 @@ int enqueue_admm_fixed(fde_problem* P, const fde_admm_opts* o, const double* yba
     CK(apply_B<float>(P, 1, P->v32[F_B], P->v32[F_Z], nullptr, P->v32[F_R], &one, s32.t1, s32.t2, st));
     CK((dot<float, float>(P, P->v32[F_Z], P->v32[F_Z], N, S_TMP0, FIN_STORE, st)));
     for (int k = 0; k < evals; ++k) {
-      // once converged, y and hence B y and the residual are unchanged: skip the products
-      const Gate g = k > 0 ? ref_gate : Gate{};
-      if (k > 0) CK(apply_B<double>(P, 0, Y, P->v64[V_BY], nullptr, nullptr, nullptr, s64.t1, s64.t2, st, g));
+      // once converged, y and hence B y and the residual are unchanged: skip the products.
+      // FDE_MIXED_DFV: double-float products except in the last evaluation, which runs in
+      // double whether or not an earlier one met tol (the accepted residual and B y are double)
+      const bool final_dfv = dfv && k == evals - 1;
+      const bool dd = o->precision == FDE_MIXED_DF || (dfv && !final_dfv);
+      const Gate g = (k > 0 && !final_dfv) ? ref_gate : Gate{};
+      if (k > 0) CK(refine_B(P, dd, 0, Y, P->v64[V_BY], nullptr, nullptr, s64.t1, s64.t2, st, g));
       CK(fold(P->v64[V_BY], P->v64[V_Q], P->v64[V_C], Y, dg.M2inv.v, dg.M1.v, last, N, P->v64[V_SD], P->v64[V_Z],
               st));
-      CK(apply_B<double>(P, 1, P->v64[V_SD], P->v64[V_R], nullptr, P->v64[V_Z], &one, s64.t1, s64.t2, st, g));
+      CK(refine_B(P, dd, 1, P->v64[V_SD], P->v64[V_R], P->v64[V_Z], &one, s64.t1, s64.t2, st, g));
       CK((dot<double, double>(P, P->v64[V_R], P->v64[V_R], N, 0, FIN_REFCHK, st, tol)));
       if (k == evals - 1) break;
       CK(to_f32_unless_conv(P, P->v64[V_R], P->v32[F_B], N, st));
@@ -794,8 +1119,13 @@ int fde_batch_admm_solve(fde_batch* b, const fde_admm_opts* o, const double* con
                          const double* yb, const double* ua, const double* ub, double* const* y, double* const* u,
                          fde_admm_stats* stats, void* stream) {
   if (!b || !valid_opts(o) || !ybar || !y || !u) return FDE_EINVAL;
-  if (o->precision != FDE_MIXED || o->max_admm < 1 || o->max_pcg < 1) return FDE_EINVAL;
+  if ((o->precision != FDE_MIXED && o->precision != FDE_MIXED_DF && o->precision != FDE_MIXED_DFV) ||
+      o->max_admm < 1 || o->max_pcg < 1)
+    return FDE_EINVAL;
   const int n = b->count;
+  for (int i = 0; i < n; ++i)
+    if (!valid_opts_for(b->probs[i], o)) return FDE_EINVAL;
+  if (o->inner_solver != 0) return FDE_EUNSUPPORTED;  // the graph solve runs PCG only
   bool same = b->exec && std::memcmp(&b->opts, o, sizeof(*o)) == 0;
   for (int i = 0; i < n; ++i) {
     if (!ybar[i] || !y[i] || !u[i]) return FDE_EINVAL;

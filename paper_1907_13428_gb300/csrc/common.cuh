@@ -4,12 +4,29 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dfloat.cuh"
+
 namespace fde {
 
 template <typename R> struct CplxOf;
 template <> struct CplxOf<float> { using type = float2; };
 template <> struct CplxOf<double> { using type = double2; };
+template <> struct CplxOf<dd> { using type = dd2; };
 template <typename R> using cplx = typename CplxOf<R>::type;
+
+// read-only cached load
+__device__ __forceinline__ float2 ldg_(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ double2 ldg_(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ dd2 ldg_(const dd2* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return dd2{dd(v.x, v.y), dd(v.z, v.w)};
+}
+
+// storage <-> compute conversions (identity unless double storage / double-float compute)
+template <typename R, typename S> __device__ __forceinline__ R cvt_in(S v) { return (R)v; }
+template <> __device__ __forceinline__ dd cvt_in<dd, double>(double v) { return to_dd(v); }
+template <typename S, typename R> __device__ __forceinline__ S cvt_out(R v) { return (S)v; }
+template <> __device__ __forceinline__ double cvt_out<double, dd>(dd v) { return to_double(v); }
 
 template <typename C> __device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) { C c; c.x = a; c.y = b; return c; }
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }

@@ -146,7 +146,7 @@ __device__ __forceinline__ void rf_compute(cplx<R> (&v)[NL][16], int t, int Ns, 
       const int step = L / (Ns * RAD);
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
-        C w = __ldg(&tw[r * k * step]);
+        C w = ldg_(&tw[r * k * step]);
         if (INV) w.y = -w.y;
 #pragma unroll
         for (int l = 0; l < NL; ++l) v[l][q * RAD + r] = cmul(v[l][q * RAD + r], w);

@@ -34,6 +34,7 @@ struct Axis {
   bool n_ok = false;  // n factors into 2, 3, 5, 7
   AxisTables<double> d;
   AxisTables<float> f;
+  AxisTables<dd> q;   // double-float copies of sym, tw2, twL, symD (L >= 16 only)
 };
 
 // Device-side gate of a transform launch in the host-sync-free solve: the
@@ -65,11 +66,13 @@ struct fde_problem {
   float* v32[12] = {};
   double2* spec64 = nullptr;
   float2* spec32 = nullptr;
+  double* mr64 = nullptr;      // saddle-point (MINRES) workspace, allocated on first use
+  float* mr32 = nullptr;
   double* partials = nullptr;  // reduction partial sums
   double* dscal = nullptr;     // device scalars
   double* hscal = nullptr;     // pinned host mirror of a few scalars
   int npartials = 0;
-  void* allocs[96] = {};
+  void* allocs[128] = {};
   int nallocs = 0;
   // FFT tile choice of the float register kernels (threads per CTA), set by fde_autotune
   int rows_nt32 = 256;  // x2 pass: 128 or 256 (row pairs per CTA = threads / (L/16))
@@ -112,6 +115,11 @@ cudaError_t setup_axis_tables(fde_problem* P, cudaStream_t st);
 template <typename R>
 cudaError_t apply_B(fde_problem* P, int transpose, const R* x, R* y, const SliceDiag* dscale,
                     const R* addv, const SliceDiag* addc, R* tmp1, R* tmp2, cudaStream_t st, Gate gate = {});
+// apply_B<double> with the transforms in double-float arithmetic (about 48
+// significand bits at float speed); vectors, epilogue and tables stay double.
+cudaError_t apply_B_df(fde_problem* P, int transpose, const double* x, double* y, const SliceDiag* dscale,
+                       const double* addv, const SliceDiag* addc, double* tmp1, double* tmp2, cudaStream_t st,
+                       Gate gate = {});
 // y = S x = M1 x + B^T (M2^-1 B x), using w (N) and tmp1, tmp2 (N) as scratch.
 template <typename R>
 cudaError_t apply_S(fde_problem* P, const SliceDiag& M1, const SliceDiag& M2inv, const R* x, R* y,
@@ -122,15 +130,19 @@ template <typename R>
 cudaError_t apply_axis_raw(fde_problem* P, int axis, const R* x, R* y, const cplx<R>* sym, int conj_sym,
                            cudaStream_t st);
 
+// apply_axis_raw<double> with the axis' own symbol in double-float arithmetic.
+cudaError_t apply_axis_raw_df(fde_problem* P, int axis, const double* x, double* y, int conj_sym, cudaStream_t st);
+
 // Times the float tile variants of the x2 and x1 passes on this problem (x, y:
 // scratch float vectors of length N) and keeps the fastest in P (toeplitz.cu).
 cudaError_t autotune_tiles(fde_problem* P, const float* x, float* y, cudaStream_t st);
 
 // Preconditioner (precond.cu): z = S~^-1 r (r and z may alias). mode 0: S~
-// (m1, m2); mode 1: (C3 C3^T)^-1 (the adjoint normal-equation preconditioner).
+// (m1, m2), sigma = m1 + |Lambda|^2 / m2 + cre Re(Lambda) (cre != 0: the matching
+// approximation S^); mode 1: (C3 C3^T)^-1 (the adjoint normal-equation preconditioner).
 template <typename R>
 cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const R* r, R* z,
-                          cplx<R>* spec, cudaStream_t st, Gate gate = {});
+                          cplx<R>* spec, cudaStream_t st, Gate gate = {}, double cre = 0.0);
 
 
 }  // namespace fde

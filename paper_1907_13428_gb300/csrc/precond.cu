@@ -100,6 +100,7 @@ struct DivArgs {
   int divide;     // 1 on the time pass
   int adjoint;    // 1: sigma = |Lambda|^2
   double m1, inv_m2, psi, inv_N;
+  double cre;     // matching approximation: sigma += cre Re(Lambda) (0: S-tilde)
   int Hp, H;
   Gate gate;  // device-side skip of the launch (host-sync-free solve)
 };
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(1024) k_prec_axis(cplx<R>* __restrict__ spec, 
       const R lr = (R)dv.psi * (a.x - b.x - d.x);
       const R li = (R)dv.psi * (a.y - b.y - d.y);
       const R mag = lr * lr + li * li;
-      const R sigma = dv.adjoint ? mag : (R)dv.m1 + mag * (R)dv.inv_m2;
+      const R sigma = dv.adjoint ? mag : (R)dv.m1 + mag * (R)dv.inv_m2 + (R)dv.cre * lr;
       const R s = (R)dv.inv_N / sigma;
       buf[e] = cscale(buf[e], s);
     }
@@ -169,7 +170,7 @@ cudaError_t precond_rows_reg_set_smem_attrs();
 
 template <typename R>
 cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const R* r, R* z, cplx<R>* spec,
-                          cudaStream_t st, Gate gate) {
+                          cudaStream_t st, Gate gate, double cre) {
   using C = cplx<R>;
   const Axis& At = P->ax[0];
   const Axis& Ax = P->ax[1];
@@ -227,6 +228,7 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
       dv.adjoint = mode;
       dv.m1 = m1;
       dv.inv_m2 = 1.0 / m2;
+      dv.cre = cre;
       dv.psi = P->psi;
       dv.inv_N = 1.0 / (double)P->N;
       dv.Hp = Hp;
@@ -267,9 +269,9 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
 }
 
 template cudaError_t apply_precond<double>(fde_problem*, double, double, int, const double*, double*, double2*,
-                                           cudaStream_t, Gate);
+                                           cudaStream_t, Gate, double);
 template cudaError_t apply_precond<float>(fde_problem*, double, double, int, const float*, float*, float2*,
-                                          cudaStream_t, Gate);
+                                          cudaStream_t, Gate, double);
 
 // Dynamic shared memory above 48 KB must be opted into per kernel.
 cudaError_t precond_set_smem_attrs() {
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(NT) k_prec_axis_reg(cplx<R>* __restrict__ spec
         const R lr = (R)dv.psi * (a.x - b.x - d.x);
         const R li = (R)dv.psi * (a.y - b.y - d.y);
         const R mag = lr * lr + li * li;
-        const R sigma = dv.adjoint ? mag : (R)dv.m1 + mag * (R)dv.inv_m2;
+        const R sigma = dv.adjoint ? mag : (R)dv.m1 + mag * (R)dv.inv_m2 + (R)dv.cre * lr;
         const R sc = pad ? (R)0 : (R)dv.inv_N / sigma;
         v[0][idx] = cscale(v[0][idx], sc);
       }

@@ -106,6 +106,11 @@ __global__ void k_to_float2(const double2* __restrict__ in, float2* __restrict__
     out[e] = make_float2((float)in[e].x, (float)in[e].y);
 }
 
+__global__ void k_to_dd2(const double2* __restrict__ in, dd2* __restrict__ out, int n) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+    out[e] = dd2{to_dd(in[e].x), to_dd(in[e].y)};
+}
+
 static int next_pow2(int n) {
   int L = 1;
   while (L < n) L <<= 1;
@@ -242,6 +247,19 @@ cudaError_t setup_axis_tables(fde_problem* P, cudaStream_t st) {
   note_launches(1);
     k_to_float2<<<(n + 255) / 256, 256, 0, st>>>(A.d.twn, A.f.twn, n);
   note_launches(1);
+    if (L >= 16) {
+      // double-float copies for the register kernels of apply_B_df
+      const double2* src[4] = {A.d.sym, A.d.tw2, A.d.twL, A.d.symD};
+      dd2** dst[4] = {&A.q.sym, &A.q.tw2, &A.q.twL, &A.q.symD};
+      const int len[4] = {2 * L, 2 * L, L, 2 * L};
+      for (int i = 0; i < 4; ++i) {
+        if (!src[i]) continue;
+        if ((e = fde_alloc(P, &p, sizeof(dd2) * len[i]))) return e;
+        *dst[i] = (dd2*)p;
+        k_to_dd2<<<(len[i] + 255) / 256, 256, 0, st>>>(src[i], *dst[i], len[i]);
+        note_launches(1);
+      }
+    }
     if ((e = cudaGetLastError())) return e;
     // scratch is reused by the next axis: wait for this one
     if ((e = cudaStreamSynchronize(st))) return e;

@@ -19,6 +19,8 @@
 // ny). For alpha_t = 1 the time term (psi/h_t)(x_t - x_{t-1}) (reversed for
 // B^T) is folded into the x1 pass; for alpha_t < 1 a third pass applies the
 // lower-triangular Toeplitz C_t along t (stride nx*ny) by the same embedding.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace fde {
@@ -211,18 +213,37 @@ __global__ void __launch_bounds__(1024) k_axis(const R* __restrict__ x, int n, i
 }
 
 // Register-resident variants (defined below) used for power-of-two L >= 16.
-template <typename R>
-cudaError_t launch_rows_reg(fde_problem* P, const R* x, int conj_sym, const cplx<R>* sym, const AxisTables<R>& T,
-                            const AxisEpi<R>& E, cudaStream_t st);
-template <typename R>
-cudaError_t launch_axis_reg(int L, const R* x, int n, long long axis_stride, long long n_inner,
+// R: transform arithmetic, S: storage of the vectors (S = R, or S = double with
+// double-float arithmetic R = dd).
+template <typename R, typename S>
+cudaError_t launch_rows_reg(fde_problem* P, const S* x, int conj_sym, const cplx<R>* sym, const AxisTables<R>& T,
+                            const AxisEpi<S>& E, cudaStream_t st);
+template <typename R, typename S>
+cudaError_t launch_axis_reg(int L, const S* x, int n, long long axis_stride, long long n_inner,
                             long long outer_stride, long long n_outer, const cplx<R>* sym, const AxisTables<R>& T,
-                            int conj_sym, const AxisEpi<R>& E, int nt_choice, cudaStream_t st);
+                            int conj_sym, const AxisEpi<S>& E, int nt_choice, cudaStream_t st);
 cudaError_t toeplitz_reg_set_smem_attrs();
 
 template <typename R> static const AxisTables<R>& tables(const Axis& A);
 template <> const AxisTables<double>& tables<double>(const Axis& A) { return A.d; }
 template <> const AxisTables<float>& tables<float>(const Axis& A) { return A.f; }
+template <> const AxisTables<dd>& tables<dd>(const Axis& A) { return A.q; }
+
+// Geometry of the strided passes: x1 lines inside each time slice, or t lines.
+static void axis_geometry(const fde_problem* P, int axis, long long* axis_stride, long long* n_inner,
+                          long long* outer_stride, long long* n_outer) {
+  if (axis == 1) {
+    *axis_stride = P->ny;
+    *n_inner = P->ny;
+    *outer_stride = (long long)P->nx * P->ny;
+    *n_outer = P->nt;
+  } else {
+    *axis_stride = (long long)P->nx * P->ny;
+    *n_inner = *axis_stride;
+    *outer_stride = 0;
+    *n_outer = 1;
+  }
+}
 
 template <typename R> static int rows_threads(int L) { return (2 * L > kEPT * 256) ? 512 : 256; }
 
@@ -232,7 +253,7 @@ static cudaError_t launch_rows(fde_problem* P, const R* x, int conj_sym, const c
   const Axis& A = P->ax[2];
   const AxisTables<R>& T = tables<R>(A);
   const int L = A.L;
-  if (L >= 16) return launch_rows_reg<R>(P, x, conj_sym, sym ? sym : T.sym, T, E, st);
+  if (L >= 16) return launch_rows_reg<R, R>(P, x, conj_sym, sym ? sym : T.sym, T, E, st);
   const int threads = rows_threads<R>(L);
   const int cap = kEPT * threads;  // complex elements per CTA
   int pairs = cap / (2 * L);
@@ -259,20 +280,10 @@ static cudaError_t launch_axis(fde_problem* P, int axis, const R* x, int conj_sy
   int pairs = cap / (2 * L);
   if (pairs < 1) pairs = 1;
   long long axis_stride, n_inner, outer_stride, n_outer;
-  if (axis == 1) {  // x1: lines along x1 inside each time slice
-    axis_stride = P->ny;
-    n_inner = P->ny;
-    outer_stride = (long long)P->nx * P->ny;
-    n_outer = P->nt;
-  } else {  // time: lines along t
-    axis_stride = (long long)P->nx * P->ny;
-    n_inner = axis_stride;
-    outer_stride = 0;
-    n_outer = 1;
-  }
+  axis_geometry(P, axis, &axis_stride, &n_inner, &outer_stride, &n_outer);
   if (L >= 16)
-    return launch_axis_reg<R>(L, x, A.n, axis_stride, n_inner, outer_stride, n_outer, sym ? sym : T.sym, T, conj_sym,
-                              E, P->axis_nt32, st);
+    return launch_axis_reg<R, R>(L, x, A.n, axis_stride, n_inner, outer_stride, n_outer, sym ? sym : T.sym, T,
+                                 conj_sym, E, P->axis_nt32, st);
   const long long total = n_outer * ((n_inner + 1) / 2);
   if (pairs > total) pairs = (int)total;
   const long long grid = (total + pairs - 1) / pairs;
@@ -283,34 +294,65 @@ static cudaError_t launch_axis(fde_problem* P, int axis, const R* x, int conj_sy
   return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t apply_B(fde_problem* P, int transpose, const R* x, R* y, const SliceDiag* dscale, const R* addv,
-                    const SliceDiag* addc, R* tmp1, R* tmp2, cudaStream_t st, Gate gate) {
+// One pass of B (S: storage type, R: transform arithmetic). `shifted`: the x1
+// symbol that carries the implicit-Euler diagonal. Axes shorter than 16 take
+// the generic kernels in the storage precision.
+template <typename S, typename R>
+static cudaError_t pass_axis(fde_problem* P, int axis, const S* x, int conj_sym, bool shifted, const AxisEpi<S>& E,
+                             cudaStream_t st) {
+  const Axis& A = P->ax[axis];
+  if constexpr (std::is_same<R, S>::value) {
+    return launch_axis<R>(P, axis, x, conj_sym, shifted ? tables<R>(A).symD : nullptr, E, st);
+  } else {
+    if (A.L < 16) return launch_axis<S>(P, axis, x, conj_sym, shifted ? tables<S>(A).symD : nullptr, E, st);
+    const AxisTables<R>& T = tables<R>(A);
+    long long axis_stride, n_inner, outer_stride, n_outer;
+    axis_geometry(P, axis, &axis_stride, &n_inner, &outer_stride, &n_outer);
+    return launch_axis_reg<R, S>(A.L, x, A.n, axis_stride, n_inner, outer_stride, n_outer, shifted ? T.symD : T.sym,
+                                 T, conj_sym, E, 0, st);
+  }
+}
+
+template <typename S, typename R>
+static cudaError_t pass_rows(fde_problem* P, const S* x, int conj_sym, const AxisEpi<S>& E, cudaStream_t st) {
+  if constexpr (std::is_same<R, S>::value) {
+    return launch_rows<R>(P, x, conj_sym, nullptr, E, st);
+  } else {
+    const Axis& A = P->ax[2];
+    if (A.L < 16) return launch_rows<S>(P, x, conj_sym, nullptr, E, st);
+    return launch_rows_reg<R, S>(P, x, conj_sym, tables<R>(A).sym, tables<R>(A), E, st);
+  }
+}
+
+template <typename S, typename R>
+static cudaError_t apply_B_t(fde_problem* P, int transpose, const S* x, S* y, const SliceDiag* dscale, const S* addv,
+                             const SliceDiag* addc, S* tmp1, S* tmp2, cudaStream_t st, Gate gate) {
   // x1 pass first (plain store), then the optional time pass, then the x2 pass,
   // whose coalesced epilogue adds the partial results, the implicit-Euler time
   // term, the per-slice diagonal and the addend.
-  AxisEpi<R> Ex{};
+  AxisEpi<S> Ex{};
   Ex.out = tmp1;
   Ex.nt = P->nt;
   Ex.plain = 1;
   Ex.gate = gate;
   // implicit Euler: the x1 symbol shifted by psi/h_t also adds +psi/h_t x_t
-  const cplx<R>* symD = P->euler ? tables<R>(P->ax[1]).symD : nullptr;
-  cudaError_t err = launch_axis<R>(P, 1, x, transpose, symD, Ex, st);
+  // (where the problem carries that symbol; otherwise the epilogue adds it)
+  const bool shifted = P->euler && tables<S>(P->ax[1]).symD != nullptr;
+  cudaError_t err = pass_axis<S, R>(P, 1, x, transpose, shifted, Ex, st);
   if (err != cudaSuccess) return err;
-  const R* acc = tmp1;
+  const S* acc = tmp1;
   if (!P->euler) {
-    AxisEpi<R> Et{};
+    AxisEpi<S> Et{};
     Et.out = tmp2;
     Et.acc = tmp1;
     Et.nt = P->nt;
     Et.t_is_axis = 1;
     Et.gate = gate;
-    err = launch_axis<R>(P, 0, x, transpose, nullptr, Et, st);
+    err = pass_axis<S, R>(P, 0, x, transpose, false, Et, st);
     if (err != cudaSuccess) return err;
     acc = tmp2;
   }
-  AxisEpi<R> E{};
+  AxisEpi<S> E{};
   E.out = y;
   E.acc = acc;
   E.nt = P->nt;
@@ -320,20 +362,32 @@ cudaError_t apply_B(fde_problem* P, int transpose, const R* x, R* y, const Slice
   if (P->euler) {
     E.xt = x;
     E.tdir = transpose ? -1 : 1;
-    E.ct = (R)(P->psi / P->ht);
-    E.nb_only = symD != nullptr;
+    E.ct = (S)(P->psi / P->ht);
+    E.nb_only = shifted;
   }
   if (dscale) {
     E.has_dsc = 1;
-    E.dsc0 = (R)dscale->v[0];
-    E.dsc1 = (R)dscale->v[1];
+    E.dsc0 = (S)dscale->v[0];
+    E.dsc1 = (S)dscale->v[1];
   }
   if (addv) {
     E.addv = addv;
-    E.addc0 = (R)addc->v[0];
-    E.addc1 = (R)addc->v[1];
+    E.addc0 = (S)addc->v[0];
+    E.addc1 = (S)addc->v[1];
   }
-  return launch_rows<R>(P, x, transpose, nullptr, E, st);
+  return pass_rows<S, R>(P, x, transpose, E, st);
+}
+
+template <typename R>
+cudaError_t apply_B(fde_problem* P, int transpose, const R* x, R* y, const SliceDiag* dscale, const R* addv,
+                    const SliceDiag* addc, R* tmp1, R* tmp2, cudaStream_t st, Gate gate) {
+  return apply_B_t<R, R>(P, transpose, x, y, dscale, addv, addc, tmp1, tmp2, st, gate);
+}
+
+cudaError_t apply_B_df(fde_problem* P, int transpose, const double* x, double* y, const SliceDiag* dscale,
+                       const double* addv, const SliceDiag* addc, double* tmp1, double* tmp2, cudaStream_t st,
+                       Gate gate) {
+  return apply_B_t<double, dd>(P, transpose, x, y, dscale, addv, addc, tmp1, tmp2, st, gate);
 }
 
 template <typename R>
@@ -356,6 +410,22 @@ cudaError_t apply_axis_raw(fde_problem* P, int axis, const R* x, R* y, const cpl
   E.plain = 1;
   if (axis == 2) return launch_rows<R>(P, x, conj_sym, sym, E, st);
   return launch_axis<R>(P, axis, x, conj_sym, sym, E, st);
+}
+
+cudaError_t apply_axis_raw_df(fde_problem* P, int axis, const double* x, double* y, int conj_sym, cudaStream_t st) {
+  const Axis& A = P->ax[axis];
+  if (A.L < 16) return apply_axis_raw<double>(P, axis, x, y, A.d.sym, conj_sym, st);
+  AxisEpi<double> E{};
+  E.out = y;
+  E.nt = P->nt;
+  E.plane = (long long)P->nx * P->ny;
+  E.rows_per_slice = P->nx;
+  E.plain = 1;
+  if (axis == 2) return launch_rows_reg<dd, double>(P, x, conj_sym, A.q.sym, A.q, E, st);
+  long long axis_stride, n_inner, outer_stride, n_outer;
+  axis_geometry(P, axis, &axis_stride, &n_inner, &outer_stride, &n_outer);
+  return launch_axis_reg<dd, double>(A.L, x, A.n, axis_stride, n_inner, outer_stride, n_outer, A.q.sym, A.q,
+                                     conj_sym, E, 0, st);
 }
 
 template cudaError_t apply_B<double>(fde_problem*, int, const double*, double*, const SliceDiag*, const double*,
@@ -395,11 +465,13 @@ namespace fde {
 // x2 axis. NT threads = PAIRS row pairs x T threads per line; thread t of a
 // pair holds positions t + r T of the pair's two half-lines. Shared memory is
 // line-major with one pad element per 16 (conflict-free exchanges).
-template <typename R, int L, int NT>
-__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const R* __restrict__ x, long long nrows,
+// R: arithmetic of the transforms; S: storage type of the vectors (R, or double
+// for double-float arithmetic).
+template <typename R, int L, int NT, typename S = R>
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const S* __restrict__ x, long long nrows,
                                                   int n, const cplx<R>* __restrict__ sym,
                                                   const cplx<R>* __restrict__ tw2, const cplx<R>* __restrict__ twL,
-                                                  int conj_sym, AxisEpi<R> E) {
+                                                  int conj_sym, AxisEpi<S> E) {
   if (gate_closed(E.gate)) return;
   using C = cplx<R>;
   constexpr int T = L / 16, PAIRS = NT / T, LS = L + L / 16;
@@ -415,11 +487,11 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const
     const int p = t + r * T;
     R a = 0, b = 0;
     if (p < n) {
-      if (ra < nrows) a = x[ra * n + p];
-      if (rb < nrows) b = x[rb * n + p];
+      if (ra < nrows) a = cvt_in<R, S>(x[ra * n + p]);
+      if (rb < nrows) b = cvt_in<R, S>(x[rb * n + p]);
     }
     v[0][r] = mk<C>(a, b);
-    v[1][r] = p < n ? cmul(v[0][r], __ldg(&tw2[p])) : mk<C>(0, 0);
+    v[1][r] = p < n ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
   }
   rf_forward<R, L, 2>(v, t, twL, at);
 #pragma unroll
@@ -427,7 +499,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const
     const int k = rf_freq<L>(t, idx);
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
-      C w = __ldg(&sym[l * L + k]);
+      C w = ldg_(&sym[l * L + k]);
       if (conj_sym) w.y = -w.y;
       v[l][idx] = cmul(v[l][idx], w);
     }
@@ -438,21 +510,21 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const
   // before any arithmetic or store, so their latencies overlap
 #pragma unroll
   for (int r0 = 0; r0 < 16; r0 += 4) {
-    EpiIn<R> ia[4], ib[4];
+    EpiIn<S> ia[4], ib[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int p = t + (r0 + k) * T;
       const bool ok = p < n;
-      ia[k] = (ok && ra < nrows) ? epi_load(E, ra * n + p, ta) : EpiIn<R>{0, 0, 0, 0};
-      ib[k] = (ok && rb < nrows) ? epi_load(E, rb * n + p, tb) : EpiIn<R>{0, 0, 0, 0};
+      ia[k] = (ok && ra < nrows) ? epi_load(E, ra * n + p, ta) : EpiIn<S>{0, 0, 0, 0};
+      ib[k] = (ok && rb < nrows) ? epi_load(E, rb * n + p, tb) : EpiIn<S>{0, 0, 0, 0};
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int p = t + (r0 + k) * T;
       if (p < n) {
-        const C res = cadd(v[0][r0 + k], cmul(v[1][r0 + k], cconj(__ldg(&tw2[p]))));
-        if (ra < nrows) epi_finish(E, ia[k], ra * n + p, ta, res.x);
-        if (rb < nrows) epi_finish(E, ib[k], rb * n + p, tb, res.y);
+        const C res = cadd(v[0][r0 + k], cmul(v[1][r0 + k], cconj(ldg_(&tw2[p]))));
+        if (ra < nrows) epi_finish(E, ia[k], ra * n + p, ta, cvt_out<S, R>(res.x));
+        if (rb < nrows) epi_finish(E, ib[k], rb * n + p, tb, cvt_out<S, R>(res.y));
       }
     }
   }
@@ -463,11 +535,11 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const
 // halves' lines side by side; the line index is XOR-swizzled by the parity of
 // the low five position bits, which separates the two position groups of every
 // half-warp into different banks.
-template <typename R, int L, int NT>
-__global__ void __launch_bounds__(NT) k_axis_reg(const R* __restrict__ x, int n, long long axis_stride,
+template <typename R, int L, int NT, typename S = R>
+__global__ void __launch_bounds__(NT) k_axis_reg(const S* __restrict__ x, int n, long long axis_stride,
                                                   long long n_inner, long long outer_stride, long long n_outer,
                                                   const cplx<R>* __restrict__ sym, const cplx<R>* __restrict__ tw2,
-                                                  const cplx<R>* __restrict__ twL, int conj_sym, AxisEpi<R> E,
+                                                  const cplx<R>* __restrict__ twL, int conj_sym, AxisEpi<S> E,
                                                   int vec2) {
   if (gate_closed(E.gate)) return;
   using C = cplx<R>;
@@ -495,16 +567,16 @@ __global__ void __launch_bounds__(NT) k_axis_reg(const R* __restrict__ x, int n,
     if (valid && p < n) {
       const long long idx = base + p * axis_stride;
       if (vec2 && has_b) {
-        const C ab = *reinterpret_cast<const C*>(x + idx);  // (c, c+1) as one aligned vector load
-        a = ab.x;
-        b = ab.y;
+        const cplx<S> ab = *reinterpret_cast<const cplx<S>*>(x + idx);  // (c, c+1) as one aligned vector load
+        a = cvt_in<R, S>(ab.x);
+        b = cvt_in<R, S>(ab.y);
       } else {
-        a = x[idx];
-        if (has_b) b = x[idx + 1];
+        a = cvt_in<R, S>(x[idx]);
+        if (has_b) b = cvt_in<R, S>(x[idx + 1]);
       }
     }
     v[0][r] = mk<C>(a, b);
-    v[1][r] = p < n ? cmul(v[0][r], __ldg(&tw2[p])) : mk<C>(0, 0);
+    v[1][r] = p < n ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
   }
   rf_forward<R, L, 2>(v, t, twL, at);
 #pragma unroll
@@ -512,7 +584,7 @@ __global__ void __launch_bounds__(NT) k_axis_reg(const R* __restrict__ x, int n,
     const int k = rf_freq<L>(t, idx);
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
-      C w = __ldg(&sym[l * L + k]);
+      C w = ldg_(&sym[l * L + k]);
       if (conj_sym) w.y = -w.y;
       v[l][idx] = cmul(v[l][idx], w);
     }
@@ -522,15 +594,15 @@ __global__ void __launch_bounds__(NT) k_axis_reg(const R* __restrict__ x, int n,
   for (int r = 0; r < 16; ++r) {
     const int p = t + r * T;
     if (valid && p < n) {
-      const C res = cadd(v[0][r], cmul(v[1][r], cconj(__ldg(&tw2[p]))));
+      const C res = cadd(v[0][r], cmul(v[1][r], cconj(ldg_(&tw2[p]))));
       const long long idx = base + p * axis_stride;
       if (E.plain && vec2 && has_b) {
-        *reinterpret_cast<C*>(E.out + idx) = res;
+        *reinterpret_cast<cplx<S>*>(E.out + idx) = mk<cplx<S>>(cvt_out<S, R>(res.x), cvt_out<S, R>(res.y));
         continue;
       }
       const int ts = E.t_is_axis ? p : (int)o;
-      axis_store(E, idx, ts, res.x);
-      if (has_b) axis_store(E, idx + 1, ts, res.y);
+      axis_store(E, idx, ts, cvt_out<S, R>(res.x));
+      if (has_b) axis_store(E, idx + 1, ts, cvt_out<S, R>(res.y));
     }
   }
 }
@@ -538,111 +610,117 @@ __global__ void __launch_bounds__(NT) k_axis_reg(const R* __restrict__ x, int n,
 template <typename R> constexpr int rows_nt() { return 256; }
 template <typename R> constexpr int axis_nt() { return sizeof(R) == 4 ? 512 : 256; }
 
-template <typename R, int L, int NT>
-static cudaError_t launch_rows_reg_LN(fde_problem* P, const R* x, int conj_sym, const cplx<R>* sym,
-                                      const AxisTables<R>& T, const AxisEpi<R>& E, cudaStream_t st) {
+template <typename R, int L, int NT, typename S>
+static cudaError_t launch_rows_reg_LN(fde_problem* P, const S* x, int conj_sym, const cplx<R>* sym,
+                                      const AxisTables<R>& T, const AxisEpi<S>& E, cudaStream_t st) {
   constexpr int PAIRS = NT / (L / 16);
   static_assert(PAIRS >= 1, "at least one row pair per CTA");
   const long long nrows = (long long)P->nt * P->nx;
   const long long npairs = (nrows + 1) / 2;
   const long long grid = (npairs + PAIRS - 1) / PAIRS;
   const size_t smem = (size_t)PAIRS * 2 * (L + L / 16) * sizeof(cplx<R>);
-  k_rows_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(x, nrows, P->ax[2].n, sym, T.tw2, T.twL, conj_sym, E);
+  k_rows_reg<R, L, NT, S><<<(unsigned)grid, NT, smem, st>>>(x, nrows, P->ax[2].n, sym, T.tw2, T.twL, conj_sym, E);
   note_launches(1);
   return cudaGetLastError();
 }
 
 // float: the tile chosen by fde_autotune (128 or 256 threads); double: 256
-template <typename R, int L>
-static cudaError_t launch_rows_reg_L(fde_problem* P, const R* x, int conj_sym, const cplx<R>* sym,
-                                     const AxisTables<R>& T, const AxisEpi<R>& E, cudaStream_t st) {
+template <typename R, int L, typename S>
+static cudaError_t launch_rows_reg_L(fde_problem* P, const S* x, int conj_sym, const cplx<R>* sym,
+                                     const AxisTables<R>& T, const AxisEpi<S>& E, cudaStream_t st) {
   if constexpr (sizeof(R) == 4 && L <= 2048) {
-    if (P->rows_nt32 == 128) return launch_rows_reg_LN<R, L, 128>(P, x, conj_sym, sym, T, E, st);
+    if (P->rows_nt32 == 128) return launch_rows_reg_LN<R, L, 128, S>(P, x, conj_sym, sym, T, E, st);
   }
-  return launch_rows_reg_LN<R, L, rows_nt<R>()>(P, x, conj_sym, sym, T, E, st);
+  return launch_rows_reg_LN<R, L, rows_nt<R>(), S>(P, x, conj_sym, sym, T, E, st);
 }
 
-template <typename R, int L, int NT>
-static cudaError_t launch_axis_reg_LN(const R* x, int n, long long axis_stride, long long n_inner,
+template <typename R, int L, int NT, typename S>
+static cudaError_t launch_axis_reg_LN(const S* x, int n, long long axis_stride, long long n_inner,
                                       long long outer_stride, long long n_outer, const cplx<R>* sym,
-                                      const AxisTables<R>& T, int conj_sym, const AxisEpi<R>& E, cudaStream_t st) {
+                                      const AxisTables<R>& T, int conj_sym, const AxisEpi<S>& E, cudaStream_t st) {
   constexpr int CP = NT / (L / 16);
   static_assert(CP >= 1, "at least one column pair per CTA");
   const long long total = n_outer * ((n_inner + 1) / 2);
   const long long grid = (total + CP - 1) / CP;
   const size_t smem = (size_t)L * 2 * CP * sizeof(cplx<R>);
-  const size_t al = 2 * sizeof(R);
+  const size_t al = 2 * sizeof(S);
   const int vec2 = ((n_inner | axis_stride | outer_stride) & 1) == 0 && ((uintptr_t)x % al) == 0 &&
                    ((uintptr_t)E.out % al) == 0;
-  k_axis_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym,
-                                                         T.tw2, T.twL, conj_sym, E, vec2);
+  k_axis_reg<R, L, NT, S><<<(unsigned)grid, NT, smem, st>>>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym,
+                                                            T.tw2, T.twL, conj_sym, E, vec2);
   note_launches(1);
   return cudaGetLastError();
 }
 
-template <typename R, int L>
-static cudaError_t launch_axis_reg_L(const R* x, int n, long long axis_stride, long long n_inner,
+template <typename R, int L, typename S>
+static cudaError_t launch_axis_reg_L(const S* x, int n, long long axis_stride, long long n_inner,
                                      long long outer_stride, long long n_outer, const cplx<R>* sym,
-                                     const AxisTables<R>& T, int conj_sym, const AxisEpi<R>& E, int nt_choice,
+                                     const AxisTables<R>& T, int conj_sym, const AxisEpi<S>& E, int nt_choice,
                                      cudaStream_t st) {
   if constexpr (sizeof(R) == 4) {
     if (nt_choice == 256)
-      return launch_axis_reg_LN<R, L, 256>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym, E,
-                                           st);
+      return launch_axis_reg_LN<R, L, 256, S>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym,
+                                              E, st);
   }
-  return launch_axis_reg_LN<R, L, axis_nt<R>()>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym,
-                                                E, st);
+  return launch_axis_reg_LN<R, L, axis_nt<R>(), S>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T,
+                                                   conj_sym, E, st);
 }
 
 #define FDE_FOR_EACH_L(M) M(16) M(32) M(64) M(128) M(256) M(512) M(1024) M(2048) M(4096)
 
-template <typename R>
-cudaError_t launch_rows_reg(fde_problem* P, const R* x, int conj_sym, const cplx<R>* sym, const AxisTables<R>& T,
-                            const AxisEpi<R>& E, cudaStream_t st) {
+template <typename R, typename S>
+cudaError_t launch_rows_reg(fde_problem* P, const S* x, int conj_sym, const cplx<R>* sym, const AxisTables<R>& T,
+                            const AxisEpi<S>& E, cudaStream_t st) {
   switch (P->ax[2].L) {
 #define FDE_CASE(LL) \
-  case LL: return launch_rows_reg_L<R, LL>(P, x, conj_sym, sym, T, E, st);
+  case LL: return launch_rows_reg_L<R, LL, S>(P, x, conj_sym, sym, T, E, st);
     FDE_FOR_EACH_L(FDE_CASE)
 #undef FDE_CASE
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <typename R>
-cudaError_t launch_axis_reg(int L, const R* x, int n, long long axis_stride, long long n_inner,
+template <typename R, typename S>
+cudaError_t launch_axis_reg(int L, const S* x, int n, long long axis_stride, long long n_inner,
                             long long outer_stride, long long n_outer, const cplx<R>* sym, const AxisTables<R>& T,
-                            int conj_sym, const AxisEpi<R>& E, int nt_choice, cudaStream_t st) {
+                            int conj_sym, const AxisEpi<S>& E, int nt_choice, cudaStream_t st) {
   switch (L) {
-#define FDE_CASE(LL)                                                                                       \
-  case LL:                                                                                                 \
-    return launch_axis_reg_L<R, LL>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym, E, \
-                                    nt_choice, st);
+#define FDE_CASE(LL)                                                                                          \
+  case LL:                                                                                                    \
+    return launch_axis_reg_L<R, LL, S>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym, E, \
+                                       nt_choice, st);
     FDE_FOR_EACH_L(FDE_CASE)
 #undef FDE_CASE
     default: return cudaErrorInvalidValue;
   }
 }
 
-template cudaError_t launch_rows_reg<double>(fde_problem*, const double*, int, const double2*,
-                                             const AxisTables<double>&, const AxisEpi<double>&, cudaStream_t);
-template cudaError_t launch_rows_reg<float>(fde_problem*, const float*, int, const float2*,
-                                            const AxisTables<float>&, const AxisEpi<float>&, cudaStream_t);
-template cudaError_t launch_axis_reg<double>(int, const double*, int, long long, long long, long long, long long,
-                                             const double2*, const AxisTables<double>&, int,
-                                             const AxisEpi<double>&, int, cudaStream_t);
-template cudaError_t launch_axis_reg<float>(int, const float*, int, long long, long long, long long, long long,
-                                            const float2*, const AxisTables<float>&, int, const AxisEpi<float>&, int,
-                                            cudaStream_t);
+template cudaError_t launch_rows_reg<double, double>(fde_problem*, const double*, int, const double2*,
+                                                     const AxisTables<double>&, const AxisEpi<double>&, cudaStream_t);
+template cudaError_t launch_rows_reg<float, float>(fde_problem*, const float*, int, const float2*,
+                                                   const AxisTables<float>&, const AxisEpi<float>&, cudaStream_t);
+template cudaError_t launch_rows_reg<dd, double>(fde_problem*, const double*, int, const dd2*, const AxisTables<dd>&,
+                                                 const AxisEpi<double>&, cudaStream_t);
+template cudaError_t launch_axis_reg<double, double>(int, const double*, int, long long, long long, long long,
+                                                     long long, const double2*, const AxisTables<double>&, int,
+                                                     const AxisEpi<double>&, int, cudaStream_t);
+template cudaError_t launch_axis_reg<float, float>(int, const float*, int, long long, long long, long long, long long,
+                                                   const float2*, const AxisTables<float>&, int,
+                                                   const AxisEpi<float>&, int, cudaStream_t);
+template cudaError_t launch_axis_reg<dd, double>(int, const double*, int, long long, long long, long long, long long,
+                                                 const dd2*, const AxisTables<dd>&, int, const AxisEpi<double>&, int,
+                                                 cudaStream_t);
 
-template <typename R>
+template <typename R, typename S = R>
 static cudaError_t set_attrs_reg() {
   const int big = 200 * 1024;
   cudaError_t e = cudaSuccess;
-#define FDE_ATTR(LL)                                                                                        \
-  if (e == cudaSuccess)                                                                                     \
-    e = cudaFuncSetAttribute(k_rows_reg<R, LL, rows_nt<R>()>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); \
-  if (e == cudaSuccess)                                                                                     \
-    e = cudaFuncSetAttribute(k_axis_reg<R, LL, axis_nt<R>()>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+#define FDE_ATTR(LL)                                                                                           \
+  if (e == cudaSuccess)                                                                                        \
+    e = cudaFuncSetAttribute(k_rows_reg<R, LL, rows_nt<R>(), S>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                             big);                                                                             \
+  if (e == cudaSuccess)                                                                                        \
+    e = cudaFuncSetAttribute(k_axis_reg<R, LL, axis_nt<R>(), S>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   FDE_FOR_EACH_L(FDE_ATTR)
 #undef FDE_ATTR
   return e;
@@ -652,6 +730,7 @@ cudaError_t toeplitz_reg_set_smem_attrs() {
   cudaError_t e = set_attrs_reg<float>();
   if (e != cudaSuccess) return e;
   if ((e = set_attrs_reg<double>()) != cudaSuccess) return e;
+  if ((e = set_attrs_reg<dd, double>()) != cudaSuccess) return e;
   const int big = 200 * 1024;
 #define FDE_ATTR2(LL)                                                                                        \
   if (e == cudaSuccess)                                                                                      \

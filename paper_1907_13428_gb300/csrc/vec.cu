@@ -234,8 +234,13 @@ __global__ void k_admm_pre(const AdmmArgs A, double* __restrict__ c, double* __r
     const double w = A.w[last], iQ = A.inv_Q[last], iM2 = A.inv_M2[last];
     const double p = A.p[i];
     const double gi = A.g ? A.g[i] : 0.0;
-    c[i] = A.rho * (w * A.ybar[i] - A.wy[i] + A.zy[i] * A.inv_delta);
-    const double b = A.rho * (-A.psi * A.wu[i] + A.psi * A.psi * A.zu[i] * A.inv_delta) + (1.0 - A.rho) * A.psi * p;
+    double cy = A.rho * (w * A.ybar[i] - A.wy[i] + A.zy[i] * A.inv_delta);
+    double b = A.rho * (-A.psi * A.wu[i] + A.psi * A.psi * A.zu[i] * A.inv_delta) + (1.0 - A.rho) * A.psi * p;
+    if (A.gen) {  // proximal pulls towards the previous iterate (Algorithm 2)
+      cy += A.ry[last] * A.yprev[i];
+      b += A.ru[last] * A.uprev[i];
+    }
+    c[i] = cy;
     bu[i] = b;
     const double r = A.psi * b * iQ - A.psi * gi + A.delta_over_rho * p;
     r0[i] = r;
@@ -261,8 +266,8 @@ __global__ void __launch_bounds__(kRedThreads) k_admm_post(const AdmmArgs A, con
     const int last = (i >= A.last_start);
     const double w = A.w[last], iQ = A.inv_Q[last], iM2 = A.inv_M2[last];
     const double yi = y[i], byi = By[i];
-    const double p = (byi + r0[i]) * iM2;
-    const double ui = (bu[i] - A.psi * p) * iQ;
+    const double p = A.given_up ? A.p[i] : (byi + r0[i]) * iM2;
+    const double ui = A.given_up ? u[i] : (bu[i] - A.psi * p) * iQ;
     const double lo_y = A.ya ? A.ya[i] : A.ya_s, hi_y = A.yb ? A.yb[i] : A.yb_s;
     const double lo_u = A.ua ? A.ua[i] : A.ua_s, hi_u = A.ub ? A.ub[i] : A.ub_s;
     const double zy = fmin(fmax(yi + A.delta * A.wy[i], lo_y), hi_y);

@@ -27,6 +27,13 @@ struct AdmmArgs {
   const double *ya, *yb, *ua, *ub;   // nullable
   double ya_s, yb_s, ua_s, ub_s;
   double *zy, *zu, *p, *wy, *wu;     // state, updated in place
+  // Algorithm 2: b_y += ry * y^j, b_u += ru * u^j (rho R_y, rho R_u per slice); gen = 0: Algorithm 1
+  int gen;
+  double ry[2], ru[2];
+  const double *yprev, *uprev;
+  // 1: the post-step reads p (in p) and u (in u) from a joint (y, u, p) solve
+  // instead of pivoting them from B y
+  int given_up;
 };
 
 int red_grid(long long n);
