@@ -3,8 +3,14 @@
 One step = one ADMM solve (Algorithm 1, fixed number of iterations, every
 sub-problem S y = rhs solved to 1e-8 relative residual) of the 1024^2 x 128
 workload (beta_x = 1.7, beta_y = 1.2, d = (2.0, 0.1), e = (0.5, 0.5),
-gamma = 1e-6, control box [-1, 1]) in MIXED precision: float FFT operator and
-preconditioner inside double iterative refinement. Inputs are resident in HBM
+gamma = 1e-6, control box [-1, 1]) in mixed precision (FDE_MIXED_DFV): float
+FFT operator and preconditioner inside iterative refinement whose residuals are
+double-float products while the next correction cannot finish the sub-problem
+and double products otherwise, so every accepted sub-problem residual (and the
+B y feeding the ADMM step) is a double product. The same solve with all
+refinement products in double (FDE_MIXED), all in double-float, in FP64
+throughout, with MINRES, Algorithm 2 and the matching preconditioner is timed
+beside it. Inputs are resident in HBM
 and each vector (1.07 GB in double) is far larger than L2, so no flush is
 needed between steps.
 
@@ -61,7 +67,10 @@ def describe(inst, admm_iters, sub_tol):
                     f"{admm_iters} iterations per solve, sub-solves to {sub_tol:g} relative residual",
         "nx": p.nx, "ny": p.ny, "nt": p.nt, "N": p.N, "beta": [p.beta_x, p.beta_y], "coef": [p.dp, p.dm, p.ep, p.em],
         "gamma": p.gamma, "box": {"ya": inst.ya, "yb": inst.yb, "ua": inst.ua, "ub": inst.ub},
-        "delta": 1.0, "rho": 1.618, "precision": "mixed (float FFT operator/preconditioner, double refinement)",
+        "delta": 1.0, "rho": 1.618,
+        "precision": "mixed: float FFT operator/preconditioner PCG inside iterative refinement; refinement residuals "
+                     "in double-float while the next correction cannot finish, in double for every accepted "
+                     "sub-problem residual and B y (FDE_MIXED_DFV)",
         "l2": "no flush: every vector (8N bytes = %.2f GB) exceeds the 126 MB L2" % (8 * p.N / 1e9),
     }
 
@@ -213,12 +222,12 @@ def run_ours(args):
     inst = workload(args.workload)
     p = inst.params
     prob = F.Problem(p)
-    tiles = prob.autotune()  # float FFT tiles picked by timing on this problem
+    tiles = {"float": prob.autotune(), "dfloat": prob.tiles(dfloat=True)}  # FFT tiles timed on this problem
     N = prob.N
     ybar = torch.as_tensor(inst.ybar.ravel(), device=dev)
     bounds = dict(ya=inst.ya, yb=inst.yb, ua=inst.ua, ub=inst.ub)
     mixed = F.AdmmOptions(delta=1.0, rho=1.618, max_admm=args.admm_iters, fixed_iters=True, inner_tol_mode=1,
-                          inner_tol=args.sub_tol, precision=F.FDE_MIXED, inner_tol_mixed=1e-4, max_pcg=500,
+                          inner_tol=args.sub_tol, precision=F.FDE_MIXED_DFV, inner_tol_mixed=1e-4, max_pcg=500,
                           max_refine=30)
     out = {k: torch.empty(N, dtype=torch.float64, device=dev) for k in ("y", "u", "p", "zu")}
 
@@ -325,7 +334,7 @@ def run_ours(args):
         extras["fp64_compare"] = {"fp64_solve_s": t64, "mixed_solve_s": value * world, "speedup": t64 / (value * world),
                                   "mixed_vs_fp64_relerr": {"y": dy, "u": du},
                                   "fp64_stats": r64["stats"], "mixed_stats": r["stats"]}
-        # the same solve with double-float refinement products (FDE_MIXED_DF)
+        # the same solve with every refinement product in double (FDE_MIXED) and in double-float (FDE_MIXED_DF)
         dfo = F.AdmmOptions(**{**mixed.__dict__, "precision": F.FDE_MIXED_DF})
         step(dfo)
         torch.cuda.synchronize()
@@ -336,9 +345,7 @@ def run_ours(args):
         tdf = a.elapsed_time(b) / 1e3
         ddy = float((out["y"] - y64c).abs().max() / y64c.abs().max())
         ddu = float((out["u"] - u64c).abs().max() / u64c.abs().max())
-        # double-float products for the evaluations that cannot be the last, double for the
-        # accepted ones (FDE_MIXED_DFV)
-        dvo = F.AdmmOptions(**{**mixed.__dict__, "precision": F.FDE_MIXED_DFV})
+        dvo = F.AdmmOptions(**{**mixed.__dict__, "precision": F.FDE_MIXED})
         step(dvo)
         torch.cuda.synchronize()
         a.record(st)
@@ -346,13 +353,14 @@ def run_ours(args):
         b.record(st)
         torch.cuda.synchronize()
         tdv = a.elapsed_time(b) / 1e3
-        extras["dfloat_compare"] = {"mixed_df_solve_s": tdf, "speedup_vs_mixed": value * world / tdf,
-                                    "mixed_df_vs_fp64_relerr": {"y": ddy, "u": ddu}, "mixed_df_stats": rdf["stats"],
-                                    "mixed_dfv_solve_s": tdv, "dfv_speedup_vs_mixed": value * world / tdv,
-                                    "mixed_dfv_vs_fp64_relerr": {
-                                        "y": float((out["y"] - y64c).abs().max() / y64c.abs().max()),
-                                        "u": float((out["u"] - u64c).abs().max() / u64c.abs().max())},
-                                    "mixed_dfv_stats": rdv["stats"]}
+        extras["refinement_products"] = {
+            "headline": "FDE_MIXED_DFV (double-float steering, double-verified)",
+            "all_double_FDE_MIXED_s": tdv, "headline_speedup_vs_all_double": tdv / (value * world),
+            "all_double_vs_fp64_relerr": {"y": float((out["y"] - y64c).abs().max() / y64c.abs().max()),
+                                          "u": float((out["u"] - u64c).abs().max() / u64c.abs().max())},
+            "all_double_stats": rdv["stats"],
+            "all_double_float_FDE_MIXED_DF_s": tdf, "all_double_float_vs_fp64_relerr": {"y": ddy, "u": ddu},
+            "all_double_float_stats": rdf["stats"]}
         # the same solve with saddle-point sub-problems by MINRES (Section 3.3.1)
         mro = F.AdmmOptions(**{**mixed.__dict__, "inner_solver": 1, "max_pcg": 2000})
         step(mro)
@@ -404,7 +412,7 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f32+double-float+f64", "data": "synthetic",
                 "config": {**describe(inst, args.admm_iters, args.sub_tol), "fft_tiles_threads": tiles},
                 "gpu_launches": launches,
                 "clocks": clk.summary(), "solve_stats": stats}
@@ -443,7 +451,7 @@ def run_batch(args):
     ua = [a for _, a, _, _ in mine]
     ub = [c for _, _, c, _ in mine]
     opts = F.AdmmOptions(delta=1.0, rho=1.618, max_admm=args.admm_iters, inner_tol=args.sub_tol,
-                         precision=F.FDE_MIXED, inner_tol_mixed=1e-4, max_refine=2, max_pcg=12)
+                         precision=F.FDE_MIXED_DFV, inner_tol_mixed=1e-4, max_refine=2, max_pcg=12)
     for _ in range(args.warmup):
         ys, us, stats = b.admm_solve(opts, ybars, ua=ua, ub=ub)
     st = torch.cuda.current_stream()
@@ -468,7 +476,7 @@ def run_batch(args):
         total_n = sum(p.N for p, _, _, _ in allp)
         line = {"metric": METRIC + " (batch workload)", "value": ms / 1e3, "unit": "s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
-                "scaling": "strong", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32+double-float+f64", "data": "synthetic",
                 "config": {"workload": f"{len(allp)} uneven instances (grids 64^2..512^2, 16..64 steps, "
                                        f"{total_n} points), ADMM {args.admm_iters} iterations each, sub-solves "
                                        f"to {args.sub_tol:g}, one CUDA-graph launch per rank per step",

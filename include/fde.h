@@ -178,14 +178,25 @@ int fde_matvec(fde_problem* prob, int op, const fde_admm_opts* opts, int precisi
 int fde_apply_factor(fde_problem* prob, int axis, int op, int precision, const void* x, void* y, void* stream);
 
 /* FFT tile autotuning: times the float transform passes of this problem with
- * each tile configuration (threads per CTA, hence lines per CTA) on the
- * problem's own sizes and keeps the fastest for all later float products of
- * `prob`. Without it a fixed default is used. fde_batch_setup calls it for
- * every instance. Synchronises `stream`. Errors: FDE_EINVAL, FDE_ECUDA. */
+ * each tile configuration (threads per CTA, hence lines per CTA, and the
+ * split-halves variant) on the problem's own sizes and keeps the fastest for all
+ * later float products of `prob`. Without it a fixed default is used.
+ * fde_batch_setup calls it for every instance. Synchronises `stream`. Errors:
+ * FDE_EINVAL, FDE_ECUDA. */
 int fde_autotune(fde_problem* prob, void* stream);
 
-/* Current tile choice: threads per CTA of the float x2 pass and x1 pass. */
-int fde_tiles(const fde_problem* prob, int* rows_threads, int* axis_threads);
+/* Current tile choice of the x2 pass and x1 pass, for precision FDE_FP32 (the
+ * float passes) or FDE_MIXED_DF (the double-float passes): threads per CTA of
+ * the kernel that holds both embedding halves of a line pair in each thread
+ * (float x2: 128 or 256, x1: 256 or 512; double-float: 256), or, negated, of the
+ * split-halves kernel whose two thread groups hold one half each (float x2: 256
+ * or 512, x1: 512 or 1024; double-float x2: 256 or 512, x1: 512). */
+int fde_tiles(const fde_problem* prob, int precision, int* rows_threads, int* axis_threads);
+
+/* Sets the tile choice (values as fde_tiles reports them; 0 keeps the current
+ * one). Errors: FDE_EINVAL (another precision, a value outside the lists above,
+ * 128 and -256 for the x2 pass when ny > 2048). */
+int fde_set_tiles(fde_problem* prob, int precision, int rows_threads, int axis_threads);
 
 /* Preconditioner z = S~^-1 r with S~ = m1 I + C_3(B)^T C_3(B) / m2 (Eq. first
  * schur complement preconditioner with C_3 of Eq. multilevel circulant

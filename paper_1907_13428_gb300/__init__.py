@@ -68,7 +68,8 @@ _SIGS = {
     "fde_apply_factor": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
     "fde_alu_peak_probe": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
     "fde_autotune": (ctypes.c_int, [_P, _P]),
-    "fde_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "fde_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "fde_set_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "fde_batch_setup": (ctypes.c_int, [ctypes.POINTER(fde_params), ctypes.c_int, ctypes.POINTER(_P), _P]),
     "fde_batch_destroy": (None, [_P]),
     "fde_batch_instance_size": (ctypes.c_longlong, [_P, ctypes.c_int]),
@@ -217,9 +218,15 @@ class Problem:
         _check(lib().fde_autotune(self._h, _stream()), "fde_autotune")
         return self.tiles()
 
-    def tiles(self):
+    def set_tiles(self, rows: int = 0, axis: int = 0, dfloat: bool = False):
+        """Fix the FFT tiles of the float (or double-float) passes (fde_set_tiles;
+        negative = split-halves kernel)."""
+        _check(lib().fde_set_tiles(self._h, FDE_MIXED_DF if dfloat else FDE_FP32, rows, axis), "fde_set_tiles")
+
+    def tiles(self, dfloat: bool = False):
         a, c = ctypes.c_int(), ctypes.c_int()
-        _check(lib().fde_tiles(self._h, ctypes.byref(a), ctypes.byref(c)), "fde_tiles")
+        _check(lib().fde_tiles(self._h, FDE_MIXED_DF if dfloat else FDE_FP32, ctypes.byref(a), ctypes.byref(c)),
+               "fde_tiles")
         return a.value, c.value
 
     def apply_factor(self, x: torch.Tensor, axis: int, op: int = FDE_OP_B, out=None,

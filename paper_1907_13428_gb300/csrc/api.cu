@@ -708,14 +708,35 @@ int fde_matvec(fde_problem* P, int op, const fde_admm_opts* o, int precision, co
 
 int fde_autotune(fde_problem* P, void* stream) {
   if (!P) return FDE_EINVAL;
-  CK(autotune_tiles(P, P->v32[F_W], P->v32[F_T1], (cudaStream_t)stream));
+  CK(autotune_tiles(P, P->v32[F_W], P->v32[F_T1], P->v64[V_W], P->v64[V_T1], (cudaStream_t)stream));
   return FDE_OK;
 }
 
-int fde_tiles(const fde_problem* P, int* rows_threads, int* axis_threads) {
-  if (!P || !rows_threads || !axis_threads) return FDE_EINVAL;
-  *rows_threads = P->rows_nt32;
-  *axis_threads = P->axis_nt32;
+int fde_set_tiles(fde_problem* P, int precision, int rows_threads, int axis_threads) {
+  if (!P || (precision != FDE_FP32 && precision != FDE_MIXED_DF)) return FDE_EINVAL;
+  const bool long_rows = P->ax[2].L > 2048;
+  bool rows_ok, axis_ok;
+  if (precision == FDE_FP32) {
+    rows_ok = rows_threads == 0 || rows_threads == 256 || rows_threads == -512 ||
+              (!long_rows && (rows_threads == 128 || rows_threads == -256));
+    axis_ok = axis_threads == 0 || axis_threads == 512 || axis_threads == 256 || axis_threads == -512 ||
+              axis_threads == -1024;
+  } else {
+    rows_ok = rows_threads == 0 || rows_threads == 256 || rows_threads == -512 || (!long_rows && rows_threads == -256);
+    axis_ok = axis_threads == 0 || axis_threads == 256 || axis_threads == -512;
+  }
+  if (!rows_ok || !axis_ok) return FDE_EINVAL;
+  int* rf = precision == FDE_FP32 ? &P->rows_nt32 : &P->rows_ntdd;
+  int* af = precision == FDE_FP32 ? &P->axis_nt32 : &P->axis_ntdd;
+  if (rows_threads) *rf = rows_threads;
+  if (axis_threads) *af = axis_threads;
+  return FDE_OK;
+}
+
+int fde_tiles(const fde_problem* P, int precision, int* rows_threads, int* axis_threads) {
+  if (!P || !rows_threads || !axis_threads || (precision != FDE_FP32 && precision != FDE_MIXED_DF)) return FDE_EINVAL;
+  *rows_threads = precision == FDE_FP32 ? P->rows_nt32 : P->rows_ntdd;
+  *axis_threads = precision == FDE_FP32 ? P->axis_nt32 : P->axis_ntdd;
   return FDE_OK;
 }
 

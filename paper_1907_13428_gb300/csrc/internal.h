@@ -77,6 +77,10 @@ struct fde_problem {
   // FFT tile choice of the float register kernels (threads per CTA), set by fde_autotune
   int rows_nt32 = 256;  // x2 pass: 128 or 256 (row pairs per CTA = threads / (L/16))
   int axis_nt32 = 512;  // x1 / t pass: 256 or 512 (column pairs per CTA = threads / (L/16))
+  // negative values: the split-halves kernels with that many threads
+  // tile choice of the double-float passes: 256 (both halves per thread) or split (-256/-512 x2, -512 x1)
+  int rows_ntdd = 256;
+  int axis_ntdd = 256;
 };
 
 namespace fde {
@@ -133,9 +137,10 @@ cudaError_t apply_axis_raw(fde_problem* P, int axis, const R* x, R* y, const cpl
 // apply_axis_raw<double> with the axis' own symbol in double-float arithmetic.
 cudaError_t apply_axis_raw_df(fde_problem* P, int axis, const double* x, double* y, int conj_sym, cudaStream_t st);
 
-// Times the float tile variants of the x2 and x1 passes on this problem (x, y:
-// scratch float vectors of length N) and keeps the fastest in P (toeplitz.cu).
-cudaError_t autotune_tiles(fde_problem* P, const float* x, float* y, cudaStream_t st);
+// Times the float and double-float tile variants of the x2 and x1 passes on this
+// problem (x, y and xd, yd: scratch vectors of length N) and keeps the fastest in
+// P (toeplitz.cu).
+cudaError_t autotune_tiles(fde_problem* P, const float* x, float* y, const double* xd, double* yd, cudaStream_t st);
 
 // Preconditioner (precond.cu): z = S~^-1 r (r and z may alias). mode 0: S~
 // (m1, m2), sigma = m1 + |Lambda|^2 / m2 + cre Re(Lambda) (cre != 0: the matching

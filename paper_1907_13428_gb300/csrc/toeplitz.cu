@@ -309,7 +309,7 @@ static cudaError_t pass_axis(fde_problem* P, int axis, const S* x, int conj_sym,
     long long axis_stride, n_inner, outer_stride, n_outer;
     axis_geometry(P, axis, &axis_stride, &n_inner, &outer_stride, &n_outer);
     return launch_axis_reg<R, S>(A.L, x, A.n, axis_stride, n_inner, outer_stride, n_outer, shifted ? T.symD : T.sym,
-                                 T, conj_sym, E, 0, st);
+                                 T, conj_sym, E, P->axis_ntdd, st);
   }
 }
 
@@ -425,7 +425,7 @@ cudaError_t apply_axis_raw_df(fde_problem* P, int axis, const double* x, double*
   long long axis_stride, n_inner, outer_stride, n_outer;
   axis_geometry(P, axis, &axis_stride, &n_inner, &outer_stride, &n_outer);
   return launch_axis_reg<dd, double>(A.L, x, A.n, axis_stride, n_inner, outer_stride, n_outer, A.q.sym, A.q,
-                                     conj_sym, E, 0, st);
+                                     conj_sym, E, P->axis_ntdd, st);
 }
 
 template cudaError_t apply_B<double>(fde_problem*, int, const double*, double*, const SliceDiag*, const double*,
@@ -607,6 +607,172 @@ __global__ void __launch_bounds__(NT) k_axis_reg(const S* __restrict__ x, int n,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Split-halves variants (float, and double-float on double vectors): the two
+// embedding halves of a line pair are transformed by two thread groups, so a
+// thread holds the 16 values of one line (half the registers of data) and twice
+// as many warps fit on an SM (float: up to 32, double-float: 16). After
+// the inverse transforms each group finishes every other position r (r % 2 ==
+// its half), taking the other half's term for those positions from shared
+// memory (the exchange buffers are free once the inverse has passed its last
+// barrier).
+// ---------------------------------------------------------------------------
+template <typename R> constexpr int split_min_blocks(int nt) { return (sizeof(R) == 4 ? 1024 : 512) / nt; }
+
+template <typename R, int L, int NT, typename S = R>
+__global__ void __launch_bounds__(NT, split_min_blocks<R>(NT)) k_rows_split(const S* __restrict__ x, long long nrows,
+                                                                           int n, const cplx<R>* __restrict__ sym,
+                                                                           const cplx<R>* __restrict__ tw2,
+                                                                           const cplx<R>* __restrict__ twL,
+                                                                           int conj_sym, AxisEpi<S> E) {
+  if (gate_closed(E.gate)) return;
+  using C = cplx<R>;
+  constexpr int T = L / 16, PAIRS = NT / (2 * T), LS = L + L / 16;
+  static_assert(PAIRS >= 1, "at least one row pair per CTA");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int pr = threadIdx.x / (2 * T);
+  const int h = (threadIdx.x / T) & 1;
+  const int t = threadIdx.x % T;
+  const long long ra = ((long long)blockIdx.x * PAIRS + pr) * 2, rb = ra + 1;
+  C* my = sm + (pr * 2 + h) * LS;
+  C* other = sm + (pr * 2 + (h ^ 1)) * LS;
+  auto at = [my](int, int pos) -> C& { return my[pos + (pos >> 4)]; };
+  C v[1][16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int p = t + r * T;
+    R a = 0, b = 0;
+    if (p < n) {
+      if (ra < nrows) a = cvt_in<R, S>(x[ra * n + p]);
+      if (rb < nrows) b = cvt_in<R, S>(x[rb * n + p]);
+    }
+    v[0][r] = mk<C>(a, b);
+    if (h) v[0][r] = p < n ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
+  }
+  rf_forward<R, L, 1>(v, t, twL, at);
+#pragma unroll
+  for (int idx = 0; idx < 16; ++idx) {
+    C w = ldg_(&sym[h * L + rf_freq<L>(t, idx)]);
+    if (conj_sym) w.y = -w.y;
+    v[0][idx] = cmul(v[0][idx], w);
+  }
+  rf_inverse<R, L, 1>(v, t, twL, at);
+  // the odd half's term is v conj(tw2[p]); hand over the positions the other group finishes
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int p = t + r * T;
+    if (h) v[0][r] = p < n ? cmul(v[0][r], cconj(ldg_(&tw2[p]))) : mk<C>(0, 0);
+    if ((r & 1) != h) my[p + (p >> 4)] = v[0][r];
+  }
+  __syncthreads();
+  const int ta = (int)(ra / E.rows_per_slice), tb = (int)(rb / E.rows_per_slice);
+#pragma unroll
+  for (int c0 = 0; c0 < 8; c0 += 4) {
+    EpiIn<S> ia[4], ib[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int p = t + (2 * (c0 + k) + h) * T;
+      const bool ok = p < n;
+      ia[k] = (ok && ra < nrows) ? epi_load(E, ra * n + p, ta) : EpiIn<S>{0, 0, 0, 0};
+      ib[k] = (ok && rb < nrows) ? epi_load(E, rb * n + p, tb) : EpiIn<S>{0, 0, 0, 0};
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int r = 2 * (c0 + k) + h;
+      const int p = t + r * T;
+      if (p < n) {
+        const C res = cadd(v[0][r], other[p + (p >> 4)]);
+        if (ra < nrows) epi_finish(E, ia[k], ra * n + p, ta, cvt_out<S, R>(res.x));
+        if (rb < nrows) epi_finish(E, ib[k], rb * n + p, tb, cvt_out<S, R>(res.y));
+      }
+    }
+  }
+}
+
+template <typename R, int L, int NT, typename S = R>
+__global__ void __launch_bounds__(NT, split_min_blocks<R>(NT)) k_axis_split(const S* __restrict__ x, int n,
+                                                                           long long axis_stride, long long n_inner,
+                                                                           long long outer_stride, long long n_outer,
+                                                                           const cplx<R>* __restrict__ sym,
+                                                                           const cplx<R>* __restrict__ tw2,
+                                                                           const cplx<R>* __restrict__ twL,
+                                                                           int conj_sym, AxisEpi<S> E, int vec2) {
+  if (gate_closed(E.gate)) return;
+  using C = cplx<R>;
+  constexpr int T = L / 16, CP = NT / (2 * T), LW = 2 * CP;
+  static_assert(CP >= 1, "at least one column pair per CTA");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  // lanes run over column pairs (coalesced), then over the two halves, then over t
+  const int cl = threadIdx.x % CP;
+  const int h = (threadIdx.x / CP) & 1;
+  const int t = threadIdx.x / (2 * CP);
+  const long long npi = (n_inner + 1) / 2;
+  const long long total = n_outer * npi;
+  const long long q = (long long)blockIdx.x * CP + cl;
+  const bool valid = q < total;
+  const long long o = valid ? q / npi : 0;
+  const long long c = valid ? 2 * (q - o * npi) : 0;
+  const long long base = o * outer_stride + c;
+  const bool has_b = valid && (c + 1 < n_inner);
+  auto slot = [cl](int l, int pos) -> int {
+    const int sw = (__popc(pos & 31) & 1) ? CP : 0;
+    return pos * LW + ((l * CP + cl) ^ sw);
+  };
+  auto at = [sm, h, slot](int, int pos) -> C& { return sm[slot(h, pos)]; };
+  C v[1][16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int p = t + r * T;
+    R a = 0, b = 0;
+    if (valid && p < n) {
+      const long long idx = base + p * axis_stride;
+      if (vec2 && has_b) {
+        const cplx<S> ab = *reinterpret_cast<const cplx<S>*>(x + idx);
+        a = cvt_in<R, S>(ab.x);
+        b = cvt_in<R, S>(ab.y);
+      } else {
+        a = cvt_in<R, S>(x[idx]);
+        if (has_b) b = cvt_in<R, S>(x[idx + 1]);
+      }
+    }
+    v[0][r] = mk<C>(a, b);
+    if (h) v[0][r] = p < n ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
+  }
+  rf_forward<R, L, 1>(v, t, twL, at);
+#pragma unroll
+  for (int idx = 0; idx < 16; ++idx) {
+    C w = ldg_(&sym[h * L + rf_freq<L>(t, idx)]);
+    if (conj_sym) w.y = -w.y;
+    v[0][idx] = cmul(v[0][idx], w);
+  }
+  rf_inverse<R, L, 1>(v, t, twL, at);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int p = t + r * T;
+    if (h) v[0][r] = p < n ? cmul(v[0][r], cconj(ldg_(&tw2[p]))) : mk<C>(0, 0);
+    if ((r & 1) != h) sm[slot(h, p)] = v[0][r];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int r = 2 * k + h;
+    const int p = t + r * T;
+    if (valid && p < n) {
+      const C res = cadd(v[0][r], sm[slot(h ^ 1, p)]);
+      const long long idx = base + p * axis_stride;
+      if (E.plain && vec2 && has_b) {
+        *reinterpret_cast<cplx<S>*>(E.out + idx) = mk<cplx<S>>(cvt_out<S, R>(res.x), cvt_out<S, R>(res.y));
+        continue;
+      }
+      const int ts = E.t_is_axis ? p : (int)o;
+      axis_store(E, idx, ts, cvt_out<S, R>(res.x));
+      if (has_b) axis_store(E, idx + 1, ts, cvt_out<S, R>(res.y));
+    }
+  }
+}
+
 template <typename R> constexpr int rows_nt() { return 256; }
 template <typename R> constexpr int axis_nt() { return sizeof(R) == 4 ? 512 : 256; }
 
@@ -624,12 +790,38 @@ static cudaError_t launch_rows_reg_LN(fde_problem* P, const S* x, int conj_sym, 
   return cudaGetLastError();
 }
 
-// float: the tile chosen by fde_autotune (128 or 256 threads); double: 256
+template <typename R, int L, int NT, typename S>
+static cudaError_t launch_rows_split_LN(fde_problem* P, const S* x, int conj_sym, const cplx<R>* sym,
+                                        const AxisTables<R>& T, const AxisEpi<S>& E, cudaStream_t st) {
+  constexpr int PAIRS = NT / (2 * (L / 16));
+  const long long nrows = (long long)P->nt * P->nx;
+  const long long npairs = (nrows + 1) / 2;
+  const long long grid = (npairs + PAIRS - 1) / PAIRS;
+  const size_t smem = (size_t)PAIRS * 2 * (L + L / 16) * sizeof(cplx<R>);
+  k_rows_split<R, L, NT, S><<<(unsigned)grid, NT, smem, st>>>(x, nrows, P->ax[2].n, sym, T.tw2, T.twL, conj_sym, E);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// float: the tile chosen by fde_autotune (128 or 256 threads, or the split-halves
+// variant with 256 or 512 threads, stored negated); double and double-float: 256
 template <typename R, int L, typename S>
 static cudaError_t launch_rows_reg_L(fde_problem* P, const S* x, int conj_sym, const cplx<R>* sym,
                                      const AxisTables<R>& T, const AxisEpi<S>& E, cudaStream_t st) {
-  if constexpr (sizeof(R) == 4 && L <= 2048) {
-    if (P->rows_nt32 == 128) return launch_rows_reg_LN<R, L, 128, S>(P, x, conj_sym, sym, T, E, st);
+  if constexpr (std::is_same<R, float>::value && std::is_same<S, float>::value) {
+    if constexpr (2 * (L / 16) <= 256) {
+      if (P->rows_nt32 == -256) return launch_rows_split_LN<R, L, 256, S>(P, x, conj_sym, sym, T, E, st);
+    }
+    if (P->rows_nt32 == -512) return launch_rows_split_LN<R, L, 512, S>(P, x, conj_sym, sym, T, E, st);
+    if constexpr (L <= 2048) {
+      if (P->rows_nt32 == 128) return launch_rows_reg_LN<R, L, 128, S>(P, x, conj_sym, sym, T, E, st);
+    }
+  }
+  if constexpr (std::is_same<R, dd>::value) {
+    if constexpr (2 * (L / 16) <= 256) {
+      if (P->rows_ntdd == -256) return launch_rows_split_LN<R, L, 256, S>(P, x, conj_sym, sym, T, E, st);
+    }
+    if (P->rows_ntdd == -512) return launch_rows_split_LN<R, L, 512, S>(P, x, conj_sym, sym, T, E, st);
   }
   return launch_rows_reg_LN<R, L, rows_nt<R>(), S>(P, x, conj_sym, sym, T, E, st);
 }
@@ -652,11 +844,42 @@ static cudaError_t launch_axis_reg_LN(const S* x, int n, long long axis_stride, 
   return cudaGetLastError();
 }
 
+template <typename R, int L, int NT, typename S>
+static cudaError_t launch_axis_split_LN(const S* x, int n, long long axis_stride, long long n_inner,
+                                        long long outer_stride, long long n_outer, const cplx<R>* sym,
+                                        const AxisTables<R>& T, int conj_sym, const AxisEpi<S>& E,
+                                        cudaStream_t st) {
+  constexpr int CP = NT / (2 * (L / 16));
+  const long long total = n_outer * ((n_inner + 1) / 2);
+  const long long grid = (total + CP - 1) / CP;
+  const size_t smem = (size_t)L * 2 * CP * sizeof(cplx<R>);
+  const size_t al = 2 * sizeof(S);
+  const int vec2 = ((n_inner | axis_stride | outer_stride) & 1) == 0 && ((uintptr_t)x % al) == 0 &&
+                   ((uintptr_t)E.out % al) == 0;
+  k_axis_split<R, L, NT, S><<<(unsigned)grid, NT, smem, st>>>(x, n, axis_stride, n_inner, outer_stride, n_outer,
+                                                              sym, T.tw2, T.twL, conj_sym, E, vec2);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 template <typename R, int L, typename S>
 static cudaError_t launch_axis_reg_L(const S* x, int n, long long axis_stride, long long n_inner,
                                      long long outer_stride, long long n_outer, const cplx<R>* sym,
                                      const AxisTables<R>& T, int conj_sym, const AxisEpi<S>& E, int nt_choice,
                                      cudaStream_t st) {
+  if constexpr (std::is_same<R, float>::value && std::is_same<S, float>::value) {
+    if (nt_choice == -512)
+      return launch_axis_split_LN<R, L, 512, S>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym,
+                                                E, st);
+    if (nt_choice == -1024)
+      return launch_axis_split_LN<R, L, 1024, S>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T,
+                                                 conj_sym, E, st);
+  }
+  if constexpr (std::is_same<R, dd>::value) {
+    if (nt_choice == -512)
+      return launch_axis_split_LN<R, L, 512, S>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym,
+                                                E, st);
+  }
   if constexpr (sizeof(R) == 4) {
     if (nt_choice == 256)
       return launch_axis_reg_LN<R, L, 256, S>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym,
@@ -731,12 +954,47 @@ cudaError_t toeplitz_reg_set_smem_attrs() {
   if (e != cudaSuccess) return e;
   if ((e = set_attrs_reg<double>()) != cudaSuccess) return e;
   if ((e = set_attrs_reg<dd, double>()) != cudaSuccess) return e;
+  {
+    const int big = 200 * 1024;
+#define FDE_ATTR6(LL)                                                                                             \
+    if (e == cudaSuccess)                                                                                         \
+      e = cudaFuncSetAttribute(k_rows_split<dd, LL, 512, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                               big);                                                                              \
+    if (e == cudaSuccess)                                                                                         \
+      e = cudaFuncSetAttribute(k_axis_split<dd, LL, 512, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                               big);
+    FDE_FOR_EACH_L(FDE_ATTR6)
+#undef FDE_ATTR6
+#define FDE_ATTR7(LL)                                                                                             \
+    if (e == cudaSuccess)                                                                                         \
+      e = cudaFuncSetAttribute(k_rows_split<dd, LL, 256, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                               big);
+    FDE_ATTR7(16) FDE_ATTR7(32) FDE_ATTR7(64) FDE_ATTR7(128) FDE_ATTR7(256) FDE_ATTR7(512) FDE_ATTR7(1024)
+    FDE_ATTR7(2048)
+#undef FDE_ATTR7
+    if (e != cudaSuccess) return e;
+  }
   const int big = 200 * 1024;
 #define FDE_ATTR2(LL)                                                                                        \
   if (e == cudaSuccess)                                                                                      \
     e = cudaFuncSetAttribute(k_axis_reg<float, LL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   FDE_FOR_EACH_L(FDE_ATTR2)
 #undef FDE_ATTR2
+#define FDE_ATTR4(LL)                                                                                        \
+  if (e == cudaSuccess)                                                                                      \
+    e = cudaFuncSetAttribute(k_rows_split<float, LL, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);       \
+  if (e == cudaSuccess)                                                                                      \
+    e = cudaFuncSetAttribute(k_axis_split<float, LL, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);       \
+  if (e == cudaSuccess)                                                                                      \
+    e = cudaFuncSetAttribute(k_axis_split<float, LL, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  FDE_FOR_EACH_L(FDE_ATTR4)
+#undef FDE_ATTR4
+#define FDE_ATTR5(LL)                                                                                        \
+  if (e == cudaSuccess)                                                                                      \
+    e = cudaFuncSetAttribute(k_rows_split<float, LL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+  FDE_ATTR5(16) FDE_ATTR5(32) FDE_ATTR5(64) FDE_ATTR5(128) FDE_ATTR5(256) FDE_ATTR5(512) FDE_ATTR5(1024)
+  FDE_ATTR5(2048)
+#undef FDE_ATTR5
 #define FDE_ATTR3(LL)                                                                                        \
   if (e == cudaSuccess)                                                                                      \
     e = cudaFuncSetAttribute(k_rows_reg<float, LL, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -746,48 +1004,60 @@ cudaError_t toeplitz_reg_set_smem_attrs() {
   return e;
 }
 
-// Tile autotuning of the float passes: each variant runs three times on the
-// problem's own sizes (after one warm-up launch) and the fastest is kept.
-cudaError_t autotune_tiles(fde_problem* P, const float* x, float* y, cudaStream_t st) {
+// Tile autotuning of the float and double-float passes: each variant runs three
+// times on the problem's own sizes (after one warm-up launch) and the fastest is
+// kept. x, y / xd, yd: scratch vectors of length N.
+cudaError_t autotune_tiles(fde_problem* P, const float* x, float* y, const double* xd, double* yd, cudaStream_t st) {
   cudaEvent_t a, b;
   cudaError_t e;
   if ((e = cudaEventCreate(&a)) != cudaSuccess) return e;
-  if ((e = cudaEventCreate(&b)) != cudaSuccess) return e;
-  auto time_it = [&](int axis, float* ms) -> cudaError_t {
-    cudaError_t r = apply_axis_raw<float>(P, axis, x, y, P->ax[axis].f.sym, 0, st);
+  if ((e = cudaEventCreate(&b)) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return e;
+  }
+  auto run = [&](int axis, bool dfl) -> cudaError_t {
+    return dfl ? apply_axis_raw_df(P, axis, xd, yd, 0, st)
+               : apply_axis_raw<float>(P, axis, x, y, P->ax[axis].f.sym, 0, st);
+  };
+  auto time_it = [&](int axis, bool dfl, float* ms) -> cudaError_t {
+    cudaError_t r = run(axis, dfl);
     if (r != cudaSuccess) return r;
     cudaEventRecord(a, st);
-    for (int k = 0; k < 3 && r == cudaSuccess; ++k) r = apply_axis_raw<float>(P, axis, x, y, P->ax[axis].f.sym, 0, st);
+    for (int k = 0; k < 3 && r == cudaSuccess; ++k) r = run(axis, dfl);
     cudaEventRecord(b, st);
     if (r == cudaSuccess) r = cudaEventSynchronize(b);
     if (r == cudaSuccess) r = cudaEventElapsedTime(ms, a, b);
     return r;
   };
-  float best = 0.f, ms = 0.f;
-  int pick = 256;
-  const int rows_cand[2] = {256, 128};
-  for (int c : rows_cand) {
-    if (c == 128 && P->ax[2].L > 2048) continue;
-    P->rows_nt32 = c;
-    if ((e = time_it(2, &ms)) != cudaSuccess) break;
-    if (c == rows_cand[0] || ms < best) {
-      best = ms;
-      pick = c;
+  // candidates of one tile field; negative: the split-halves variant with that many threads
+  auto tune = [&](int* field, const int* cand, int nc, int axis, bool dfl, bool short_only_mask) -> cudaError_t {
+    float best = 0.f, ms = 0.f;
+    int pick = cand[0];
+    bool first = true;
+    for (int i = 0; i < nc; ++i) {
+      const int c = cand[i];
+      // 128-thread and 256-thread split x2 tiles need a line of at most 2048
+      if (short_only_mask && (c == 128 || c == -256) && P->ax[axis].L > 2048) continue;
+      *field = c;
+      const cudaError_t r = time_it(axis, dfl, &ms);
+      if (r != cudaSuccess) return r;
+      if (first || ms < best) {
+        best = ms;
+        pick = c;
+        first = false;
+      }
     }
-  }
-  P->rows_nt32 = pick;
-  const int axis_cand[2] = {512, 256};
-  pick = 512;
-  for (int c : axis_cand) {
-    if (e != cudaSuccess) break;
-    P->axis_nt32 = c;
-    if ((e = time_it(1, &ms)) != cudaSuccess) break;
-    if (c == axis_cand[0] || ms < best) {
-      best = ms;
-      pick = c;
-    }
-  }
-  P->axis_nt32 = pick;
+    *field = pick;
+    return cudaSuccess;
+  };
+  const int rows32[4] = {256, 128, -256, -512};
+  const int axis32[4] = {512, 256, -512, -1024};
+  const int rowsdd[3] = {256, -512, -256};
+  const int axisdd[2] = {256, -512};
+  if (e == cudaSuccess) e = tune(&P->rows_nt32, rows32, 4, 2, false, true);
+  if (e == cudaSuccess) e = tune(&P->axis_nt32, axis32, 4, 1, false, false);
+  if (e == cudaSuccess) e = tune(&P->rows_ntdd, rowsdd, 3, 2, true, true);
+  if (e == cudaSuccess) e = tune(&P->axis_ntdd, axisdd, 2, 1, true, false);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   return e;

@@ -228,3 +228,55 @@ def test_batch_mixed_dfv_matches_oracle():
         assert relerr(host(y), ref.y) < 1e-8
         assert relerr(host(u), ref.u) < 1e-8
     b.close()
+
+
+@pytest.mark.parametrize("tiles", [(256, 256), (-512, -512), (-256, -512)])
+@pytest.mark.parametrize("dims", [(17, 33, 6), (64, 64, 4), (100, 50, 3), (31, 200, 2), (2, 1100, 2)])
+def test_every_dfloat_tile_matches_oracle(dims, tiles):
+    """Both double-float tile variants (both halves per thread, split halves) of
+    the x2 and x1 passes, with the epilogue, against the oracle."""
+    need_gpu()
+    F = lib()
+    nx, ny, nt = dims
+    p = params(nx, ny, nt)
+    prob = F.Problem(p)
+    rows, axis = tiles
+    if ny > 2048 and rows == -256:
+        rows = 0
+    prob.set_tiles(rows, axis, dfloat=True)
+    assert prob.tiles(dfloat=True)[1] == axis
+    x = fi.random_field(47, (nt, nx, ny))
+    for op, tr in ((F.FDE_OP_B, False), (F.FDE_OP_BT, True)):
+        got = host(prob.matvec(dev(x), op, dfloat=True))
+        assert relerr(got, O.apply_B(p, x, transpose=tr)) < 1e-11
+    prob.close()
+
+
+def test_dfv_full_size_against_mixed_and_fp64():
+    """1024^2 x 128, the benchmark's configuration (one ADMM iteration, sub-solves
+    to 1e-8): the FDE_MIXED_DFV solve meets every sub-problem target with a double
+    residual, keeps the box, and agrees with the all-double refinement and with the
+    all-FP64 solve to the accuracy the 1e-8 sub-solve tolerance allows."""
+    need_gpu()
+    F = lib()
+    inst = fi.config_large()
+    prob = F.Problem(inst.params)
+    ybar = dev(inst.ybar)
+    base = dict(delta=1.0, rho=1.618, max_admm=1, fixed_iters=True, inner_tol_mode=1, inner_tol=1e-8,
+                inner_tol_mixed=1e-4, max_pcg=500, max_refine=30)
+    ys = {}
+    for prec in (F.FDE_MIXED_DFV, F.FDE_MIXED, F.FDE_FP64):
+        r = prob.admm_solve(F.AdmmOptions(**base, precision=prec), ybar, ua=inst.ua, ub=inst.ub, allow_noconv=True)
+        assert r["stats"]["max_sub_relres"] <= 1e-8, (prec, r["stats"])
+        ys[prec] = r["y"].clone()
+        if prec == F.FDE_MIXED_DFV:
+            zu = r["zu"]
+            assert bool(torch.all(zu >= inst.ua)) and bool(torch.all(zu <= inst.ub))
+            assert bool(torch.all(torch.isfinite(r["y"])))
+        del r
+    scale = float(ys[F.FDE_FP64].abs().max())
+    assert float((ys[F.FDE_MIXED_DFV] - ys[F.FDE_MIXED]).abs().max()) / scale < 1e-6
+    assert float((ys[F.FDE_MIXED_DFV] - ys[F.FDE_FP64]).abs().max()) / scale < 1e-6
+    del ys
+    prob.close()
+    torch.cuda.empty_cache()

@@ -177,9 +177,52 @@ def test_autotuned_tiles_keep_parity(dims):
     p = params(nx, ny, nt)
     prob = F.Problem(p)
     rows, axis = prob.autotune()
-    assert rows in (128, 256) and axis in (256, 512)
+    assert rows in (128, 256, -256, -512) and axis in (256, 512, -512, -1024)
+    rd, ad = prob.tiles(dfloat=True)
+    assert rd in (256, -256, -512) and ad in (256, -512)
+    assert relerr(host(prob.matvec(dev(fi.random_field(3, (nt, nx, ny))), dfloat=True)),
+                  O.apply_B(p, fi.random_field(3, (nt, nx, ny)))) < 1e-11
     x = fi.random_field(31, (nt, nx, ny))
     ref = O.apply_B(p, x)
     assert relerr(host(prob.matvec(dev(x, torch.float32))), ref) < 2e-5
     assert relerr(host(prob.matvec(dev(x))), ref) < 1e-12
+    prob.close()
+
+
+@pytest.mark.parametrize("tiles", [(128, 256), (256, 512), (-256, -512), (-512, -1024)])
+@pytest.mark.parametrize("dims", [(7, 5, 3), (33, 17, 6), (64, 64, 4), (100, 50, 3), (17, 300, 2), (2, 1100, 2)])
+def test_every_float_tile_matches_oracle(dims, tiles):
+    """Each float tile variant (both halves per thread, or split halves) of the x2
+    and x1 passes: B, B^T and S against the oracle, with the epilogue."""
+    need_gpu()
+    F = lib()
+    nx, ny, nt = dims
+    p = params(nx, ny, nt)
+    prob = F.Problem(p)
+    rows, axis = tiles
+    if ny > 2048 and rows in (128, -256):
+        rows = 0
+    prob.set_tiles(rows, axis)
+    x = fi.random_field(37, (nt, nx, ny))
+    for op, tr in ((F.FDE_OP_B, False), (F.FDE_OP_BT, True)):
+        assert relerr(host(prob.matvec(dev(x, torch.float32), op)), O.apply_B(p, x, transpose=tr)) < 2e-5
+    fo = F.AdmmOptions(delta=0.7, rho=1.4)
+    got = host(prob.matvec(dev(x, torch.float32), F.FDE_OP_S, fo))
+    assert relerr(got, O.apply_S(p, O.AdmmOptions(delta=0.7, rho=1.4), x)) < 2e-5
+    for axis_ in (1, 2):
+        X, Y = O.space_matrices(p)
+        M, along = (X, O.along_x1) if axis_ == 1 else (Y, O.along_x2)
+        ref = -O.psi_scale(p) * along(M, x)
+        assert relerr(host(prob.apply_factor(dev(x, torch.float32), axis_)), ref) < 2e-5
+    prob.close()
+
+
+def test_set_tiles_rejects_unknown_values():
+    need_gpu()
+    F = lib()
+    prob = F.Problem(params(8, 8, 2))
+    for bad in ((64, 0), (0, 1000), (-128, 0)):
+        with pytest.raises(F.FdeError) as e:
+            prob.set_tiles(*bad)
+        assert e.value.status == F.FDE_EINVAL
     prob.close()
