@@ -294,20 +294,33 @@ def run_ours(args):
         hbm, src = peaks()
         fp64_peak = F.alu_peak(F.FDE_FP64)
         fp32_peak = F.alu_peak(F.FDE_FP32)
-        # dominant kernel of the mixed solve (launch-list share): the double x2 Toeplitz pass.
         # Algorithmic flops per point of one pass: 4 transforms of length L per complex
         # line of two real lines at 5 L log2 L (10 log2 L per point) plus 13 for the
-        # twists, symbol products and the halves' combination.
+        # twists, symbol products and the halves' combination. Algorithmic bytes of a
+        # pass: read x, write y.
         L = 1
         while L < p.ny:
             L *= 2
         flops = (10.0 * math.log2(L) + 13.0) * N
+        # dominant kernel of the solve (launch-list share): the float x2 Toeplitz pass of the
+        # PCG operator. Its arithmetic roof (flops at the measured float FMA rate) lies above
+        # its memory roof (8N bytes at the measured copy bandwidth), so it is reported as ALU-bound.
+        ach32 = flops / (t_x2_32 * 1e-3) / 1e12
+        gbs32 = 8.0 * N / (t_x2_32 * 1e-3) / 1e9
+        extras["roofline"] = {"bound": "alu", "achieved": ach32, "peak": fp32_peak, "unit": "TFLOP/s",
+                              "frac": ach32 / fp32_peak, "traffic": traffic_for("k_rows_reg_float_1024"),
+                              "kernel": "float x2 Toeplitz pass (k_rows_reg<float,1024>, autotuned tile; one launch)",
+                              "flops_per_launch": flops, "ms": t_x2_32,
+                              "peak_source": "measured: fde_alu_peak_probe FMA chains, float",
+                              "hbm_view": {"alg_bytes_per_launch": 8.0 * N, "gbs": gbs32, "peak": hbm,
+                                           "frac": gbs32 / hbm, "peak_source": src}}
+        # the double x2 pass of the verifying refinement evaluations
         achieved = flops / (t_x2_64 * 1e-3) / 1e12
-        extras["roofline"] = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                              "frac": achieved / fp64_peak, "traffic": traffic_for("k_rows_reg_double_1024"),
-                              "kernel": "k_rows_reg<double,1024>: x2 Toeplitz pass in double (one launch)",
-                              "flops_per_launch": flops, "ms": t_x2_64,
-                              "peak_source": "measured: fde_alu_peak_probe FMA chains, double"}
+        extras["roofline_fp64"] = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                                   "frac": achieved / fp64_peak, "traffic": traffic_for("k_rows_reg_double_1024"),
+                                   "kernel": "k_rows_reg<double,1024>: x2 Toeplitz pass in double (one launch)",
+                                   "flops_per_launch": flops, "ms": t_x2_64,
+                                   "peak_source": "measured: fde_alu_peak_probe FMA chains, double"}
         alg = 8.0 * N  # read x, write y (float)
         extras["matvec"] = {"kernel": "Toeplitz-FFT matvec y = B x, float (x1 pass + x2 pass)", "ms": t_b32,
                             "alg_bytes": alg, "gbs": alg / (t_b32 * 1e-3) / 1e9, "hbm_peak": hbm,
@@ -498,6 +511,7 @@ def run_kernels(args):
     import paper_1907_13428_gb300 as F
     inst = workload(args.workload)
     prob = F.Problem(inst.params)
+    prob.autotune()  # the tiles the solve uses
     x64 = torch.as_tensor(inst.ybar.ravel(), device="cuda")
     x32 = x64.float()
     y64 = torch.empty_like(x64)
@@ -519,7 +533,31 @@ def run_kernels(args):
         b.record()
         torch.cuda.synchronize()
         out[name] = a.elapsed_time(b) / max(1, args.steps)
-    print(json.dumps({"kernels_ms": out, "workload": describe(inst, 0, 0)["workload"], "N": prob.N}), flush=True)
+    tiles = {"float": prob.tiles(), "dfloat": prob.tiles(dfloat=True)}
+    # every float tile of the two passes (threads per CTA)
+    sweep = {}
+    long_rows = prob.shape[2] > 2048
+    for rows, axis in ((256, 512), (128, 256)):
+        if long_rows and rows == 128:
+            continue
+        prob.set_tiles(rows, axis)
+        for name, fn in (("x2", lambda: prob.apply_factor(x32, 2, out=y32)),
+                         ("x1", lambda: prob.apply_factor(x32, 1, out=y32))):
+            if name == "x1" and axis == 0:
+                continue
+            fn()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(3):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            sweep[f"{name}_f32_tile_{rows if name == 'x2' else axis}"] = a.elapsed_time(b) / 3
+    prob.set_tiles(*tiles["float"])
+    print(json.dumps({"kernels_ms": out, "float_tile_sweep_ms": sweep, "workload": describe(inst, 0, 0)["workload"],
+                      "N": prob.N, "tiles": tiles}), flush=True)
     prob.close()
 
 

@@ -189,8 +189,8 @@ int fde_autotune(fde_problem* prob, void* stream);
  * float passes) or FDE_MIXED_DF (the double-float passes): threads per CTA of
  * the kernel that holds both embedding halves of a line pair in each thread
  * (float x2: 128 or 256, x1: 256 or 512; double-float: 256), or, negated, of the
- * split-halves kernel whose two thread groups hold one half each (float x2: 256
- * or 512, x1: 512 or 1024; double-float x2: 256 or 512, x1: 512). */
+ * double-float split-halves kernel whose two thread groups hold one half each
+ * (x2: 256 or 512, x1: 512). */
 int fde_tiles(const fde_problem* prob, int precision, int* rows_threads, int* axis_threads);
 
 /* Sets the tile choice (values as fde_tiles reports them; 0 keeps the current

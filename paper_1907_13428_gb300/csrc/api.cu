@@ -717,10 +717,8 @@ int fde_set_tiles(fde_problem* P, int precision, int rows_threads, int axis_thre
   const bool long_rows = P->ax[2].L > 2048;
   bool rows_ok, axis_ok;
   if (precision == FDE_FP32) {
-    rows_ok = rows_threads == 0 || rows_threads == 256 || rows_threads == -512 ||
-              (!long_rows && (rows_threads == 128 || rows_threads == -256));
-    axis_ok = axis_threads == 0 || axis_threads == 512 || axis_threads == 256 || axis_threads == -512 ||
-              axis_threads == -1024;
+    rows_ok = rows_threads == 0 || rows_threads == 256 || (!long_rows && rows_threads == 128);
+    axis_ok = axis_threads == 0 || axis_threads == 512 || axis_threads == 256;
   } else {
     rows_ok = rows_threads == 0 || rows_threads == 256 || rows_threads == -512 || (!long_rows && rows_threads == -256);
     axis_ok = axis_threads == 0 || axis_threads == 256 || axis_threads == -512;

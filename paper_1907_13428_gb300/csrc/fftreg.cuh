@@ -18,6 +18,10 @@
 
 namespace fde {
 
+// Twiddle-table access through the read-only cache (overloadable for other
+// table placements).
+template <typename C> __device__ __forceinline__ C tw_get(const C* __restrict__ p, int i) { return ldg_(p + i); }
+
 template <int L> struct RfShape {
   static constexpr int T = L / 16;
   static constexpr int P = (L <= 16) ? 1 : (L <= 256 ? 2 : 3);
@@ -133,8 +137,8 @@ __device__ __forceinline__ void dftR(C* v) {
 
 // One pass' arithmetic on the 16 values of thread t: butterflies q < 16/RAD,
 // j = t + T q, twiddles W_{Ns RAD}^{r (j mod Ns)} from tw = W_L^m, then DFT.
-template <typename R, int L, int RAD, bool INV, int NL>
-__device__ __forceinline__ void rf_compute(cplx<R> (&v)[NL][16], int t, int Ns, const cplx<R>* __restrict__ tw) {
+template <typename R, int L, int RAD, bool INV, int NL, class Tab>
+__device__ __forceinline__ void rf_compute(cplx<R> (&v)[NL][16], int t, int Ns, Tab tw) {
   using C = cplx<R>;
   constexpr int T = L / 16;
   constexpr int B = 16 / RAD;
@@ -146,7 +150,7 @@ __device__ __forceinline__ void rf_compute(cplx<R> (&v)[NL][16], int t, int Ns, 
       const int step = L / (Ns * RAD);
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
-        C w = ldg_(&tw[r * k * step]);
+        C w = tw_get(tw, r * k * step);
         if (INV) w.y = -w.y;
 #pragma unroll
         for (int l = 0; l < NL; ++l) v[l][q * RAD + r] = cmul(v[l][q * RAD + r], w);
@@ -185,8 +189,8 @@ __device__ __forceinline__ void rf_exchange(cplx<R> (&v)[NL][16], int t, int Ns,
 }
 
 // Forward transform: positions t + r T  ->  t + T q + r L/RL.
-template <typename R, int L, int NL, class At>
-__device__ __forceinline__ void rf_forward(cplx<R> (&v)[NL][16], int t, const cplx<R>* __restrict__ tw, At at) {
+template <typename R, int L, int NL, class At, class Tab>
+__device__ __forceinline__ void rf_forward(cplx<R> (&v)[NL][16], int t, Tab tw, At at) {
   using S = RfShape<L>;
   if constexpr (S::P == 1) {
     rf_compute<R, L, 16, false, NL>(v, t, 1, tw);
@@ -204,8 +208,8 @@ __device__ __forceinline__ void rf_forward(cplx<R> (&v)[NL][16], int t, const cp
 }
 
 // Inverse (unnormalised) transform: positions t + T q + r L/RL  ->  t + r T.
-template <typename R, int L, int NL, class At>
-__device__ __forceinline__ void rf_inverse(cplx<R> (&v)[NL][16], int t, const cplx<R>* __restrict__ tw, At at) {
+template <typename R, int L, int NL, class At, class Tab>
+__device__ __forceinline__ void rf_inverse(cplx<R> (&v)[NL][16], int t, Tab tw, At at) {
   using S = RfShape<L>;
   if constexpr (S::P == 1) {
     rf_compute<R, L, 16, true, NL>(v, t, 1, tw);

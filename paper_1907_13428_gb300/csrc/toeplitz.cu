@@ -608,10 +608,12 @@ __global__ void __launch_bounds__(NT) k_axis_reg(const S* __restrict__ x, int n,
 }
 
 // ---------------------------------------------------------------------------
-// Split-halves variants (float, and double-float on double vectors): the two
+// Split-halves variants (used for double-float on double vectors): the two
 // embedding halves of a line pair are transformed by two thread groups, so a
 // thread holds the 16 values of one line (half the registers of data) and twice
-// as many warps fit on an SM (float: up to 32, double-float: 16). After
+// as many warps fit on an SM (16 at 128 registers). For float the kernels that
+// hold both halves per thread are faster (measured), so only the double-float
+// instantiations are launched. After
 // the inverse transforms each group finishes every other position r (r % 2 ==
 // its half), taking the other half's term for those positions from shared
 // memory (the exchange buffers are free once the inverse has passed its last
@@ -809,10 +811,6 @@ template <typename R, int L, typename S>
 static cudaError_t launch_rows_reg_L(fde_problem* P, const S* x, int conj_sym, const cplx<R>* sym,
                                      const AxisTables<R>& T, const AxisEpi<S>& E, cudaStream_t st) {
   if constexpr (std::is_same<R, float>::value && std::is_same<S, float>::value) {
-    if constexpr (2 * (L / 16) <= 256) {
-      if (P->rows_nt32 == -256) return launch_rows_split_LN<R, L, 256, S>(P, x, conj_sym, sym, T, E, st);
-    }
-    if (P->rows_nt32 == -512) return launch_rows_split_LN<R, L, 512, S>(P, x, conj_sym, sym, T, E, st);
     if constexpr (L <= 2048) {
       if (P->rows_nt32 == 128) return launch_rows_reg_LN<R, L, 128, S>(P, x, conj_sym, sym, T, E, st);
     }
@@ -867,14 +865,6 @@ static cudaError_t launch_axis_reg_L(const S* x, int n, long long axis_stride, l
                                      long long outer_stride, long long n_outer, const cplx<R>* sym,
                                      const AxisTables<R>& T, int conj_sym, const AxisEpi<S>& E, int nt_choice,
                                      cudaStream_t st) {
-  if constexpr (std::is_same<R, float>::value && std::is_same<S, float>::value) {
-    if (nt_choice == -512)
-      return launch_axis_split_LN<R, L, 512, S>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym,
-                                                E, st);
-    if (nt_choice == -1024)
-      return launch_axis_split_LN<R, L, 1024, S>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T,
-                                                 conj_sym, E, st);
-  }
   if constexpr (std::is_same<R, dd>::value) {
     if (nt_choice == -512)
       return launch_axis_split_LN<R, L, 512, S>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym,
@@ -980,21 +970,6 @@ cudaError_t toeplitz_reg_set_smem_attrs() {
     e = cudaFuncSetAttribute(k_axis_reg<float, LL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   FDE_FOR_EACH_L(FDE_ATTR2)
 #undef FDE_ATTR2
-#define FDE_ATTR4(LL)                                                                                        \
-  if (e == cudaSuccess)                                                                                      \
-    e = cudaFuncSetAttribute(k_rows_split<float, LL, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);       \
-  if (e == cudaSuccess)                                                                                      \
-    e = cudaFuncSetAttribute(k_axis_split<float, LL, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);       \
-  if (e == cudaSuccess)                                                                                      \
-    e = cudaFuncSetAttribute(k_axis_split<float, LL, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  FDE_FOR_EACH_L(FDE_ATTR4)
-#undef FDE_ATTR4
-#define FDE_ATTR5(LL)                                                                                        \
-  if (e == cudaSuccess)                                                                                      \
-    e = cudaFuncSetAttribute(k_rows_split<float, LL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  FDE_ATTR5(16) FDE_ATTR5(32) FDE_ATTR5(64) FDE_ATTR5(128) FDE_ATTR5(256) FDE_ATTR5(512) FDE_ATTR5(1024)
-  FDE_ATTR5(2048)
-#undef FDE_ATTR5
 #define FDE_ATTR3(LL)                                                                                        \
   if (e == cudaSuccess)                                                                                      \
     e = cudaFuncSetAttribute(k_rows_reg<float, LL, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -1036,7 +1011,7 @@ cudaError_t autotune_tiles(fde_problem* P, const float* x, float* y, const doubl
     bool first = true;
     for (int i = 0; i < nc; ++i) {
       const int c = cand[i];
-      // 128-thread and 256-thread split x2 tiles need a line of at most 2048
+      // the 128-thread and 256-thread split x2 tiles need a line of at most 2048
       if (short_only_mask && (c == 128 || c == -256) && P->ax[axis].L > 2048) continue;
       *field = c;
       const cudaError_t r = time_it(axis, dfl, &ms);
@@ -1050,12 +1025,12 @@ cudaError_t autotune_tiles(fde_problem* P, const float* x, float* y, const doubl
     *field = pick;
     return cudaSuccess;
   };
-  const int rows32[4] = {256, 128, -256, -512};
-  const int axis32[4] = {512, 256, -512, -1024};
+  const int rows32[2] = {256, 128};
+  const int axis32[2] = {512, 256};
   const int rowsdd[3] = {256, -512, -256};
   const int axisdd[2] = {256, -512};
-  if (e == cudaSuccess) e = tune(&P->rows_nt32, rows32, 4, 2, false, true);
-  if (e == cudaSuccess) e = tune(&P->axis_nt32, axis32, 4, 1, false, false);
+  if (e == cudaSuccess) e = tune(&P->rows_nt32, rows32, 2, 2, false, true);
+  if (e == cudaSuccess) e = tune(&P->axis_nt32, axis32, 2, 1, false, false);
   if (e == cudaSuccess) e = tune(&P->rows_ntdd, rowsdd, 3, 2, true, true);
   if (e == cudaSuccess) e = tune(&P->axis_ntdd, axisdd, 2, 1, true, false);
   cudaEventDestroy(a);

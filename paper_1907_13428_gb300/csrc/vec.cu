@@ -37,6 +37,26 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
   return v;
 }
 
+// Block maximum of non-negative values held as their bit patterns: for
+// non-negative doubles the integer order is the numeric order, and infinities
+// and NaNs (exponent all ones) compare above every finite value.
+__device__ __forceinline__ long long block_max_bits(long long v, long long* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
+  __syncthreads();
+  return v;
+}
+
+__device__ __forceinline__ long long abs_bits(double x) {
+  return __double_as_longlong(x) & 0x7fffffffffffffffLL;
+}
+
 int red_grid(long long n) {
   long long g = (n + 4LL * kRedThreads - 1) / (4LL * kRedThreads);
   if (g < 1) g = 1;
@@ -228,23 +248,32 @@ __global__ void k_copy(R* __restrict__ dst, const R* __restrict__ src, long long
 // ---------------------------------------------------------------------------
 __global__ void k_admm_pre(const AdmmArgs A, double* __restrict__ c, double* __restrict__ bu, double* __restrict__ r0,
                            double* __restrict__ q) {
+  // Coefficients folded once per thread: on this GPU the double pipe, not memory,
+  // bounds these streaming steps, so each element costs fused multiply-adds only
+  // (reciprocals instead of divides).
+  const double cyb[2] = {A.rho * A.w[0], A.rho * A.w[1]};
+  const double rod = A.rho * A.inv_delta;
+  const double k1 = -A.rho * A.psi, k2 = A.rho * A.psi * A.psi * A.inv_delta, k3 = (1.0 - A.rho) * A.psi;
+  const double k4[2] = {A.psi * A.inv_Q[0], A.psi * A.inv_Q[1]};
+  const double omr = 1.0 - A.rho;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.n; i += (long long)gridDim.x * blockDim.x) {
     const int last = (i >= A.last_start);
-    // reciprocals instead of divides: double divides are slow on this GPU
-    const double w = A.w[last], iQ = A.inv_Q[last], iM2 = A.inv_M2[last];
     const double p = A.p[i];
-    const double gi = A.g ? A.g[i] : 0.0;
-    double cy = A.rho * (w * A.ybar[i] - A.wy[i] + A.zy[i] * A.inv_delta);
-    double b = A.rho * (-A.psi * A.wu[i] + A.psi * A.psi * A.zu[i] * A.inv_delta) + (1.0 - A.rho) * A.psi * p;
+    // c = rho (w ybar - w_y + z_y / delta), b_u = rho (-psi w_u + psi^2 z_u / delta) + (1 - rho) psi p
+    double cy = fma(cyb[last], A.ybar[i], fma(-A.rho, A.wy[i], rod * A.zy[i]));
+    double b = fma(k1, A.wu[i], fma(k2, A.zu[i], k3 * p));
     if (A.gen) {  // proximal pulls towards the previous iterate (Algorithm 2)
-      cy += A.ry[last] * A.yprev[i];
-      b += A.ru[last] * A.uprev[i];
+      cy = fma(A.ry[last], A.yprev[i], cy);
+      b = fma(A.ru[last], A.uprev[i], b);
     }
     c[i] = cy;
     bu[i] = b;
-    const double r = A.psi * b * iQ - A.psi * gi + A.delta_over_rho * p;
+    // r0 = psi Q^-1 b_u - psi g + (delta/rho) p,  q = (1 - rho) p - M2^-1 r0
+    double r = A.delta_over_rho * p;
+    if (A.g) r = fma(-A.psi, A.g[i], r);
+    r = fma(k4[last], b, r);
     r0[i] = r;
-    q[i] = (1.0 - A.rho) * p - r * iM2;
+    q[i] = fma(-A.inv_M2[last], r, omr * p);
   }
 }
 
@@ -260,45 +289,57 @@ __global__ void __launch_bounds__(kRedThreads) k_admm_post(const AdmmArgs A, con
                                                             const double* __restrict__ r0, double* __restrict__ u,
                                                             double* __restrict__ partials, int np) {
   __shared__ double sh[32];
-  double m_eq = 0.0, m_y = 0.0, m_u = 0.0, obj = 0.0;
-  bool bad = false;
+  __shared__ long long shl[32];
+  // residual maxima on bit patterns (integer pipe); non-finite values show up as
+  // maxima with an all-ones exponent; the objective's two sums per weight class
+  long long m_eq = 0, m_y = 0, m_u = 0;
+  double oy = 0.0, ou = 0.0, oyl = 0.0, oul = 0.0;
+  const double rpsi = A.rho_over_delta * A.psi;
+  const double piq[2] = {A.psi * A.inv_Q[0], A.psi * A.inv_Q[1]};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.n; i += (long long)gridDim.x * blockDim.x) {
     const int last = (i >= A.last_start);
-    const double w = A.w[last], iQ = A.inv_Q[last], iM2 = A.inv_M2[last];
+    const double iM2 = A.inv_M2[last];
     const double yi = y[i], byi = By[i];
-    const double p = A.given_up ? A.p[i] : (byi + r0[i]) * iM2;
-    const double ui = A.given_up ? u[i] : (bu[i] - A.psi * p) * iQ;
+    const double p = A.given_up ? A.p[i] : iM2 * (byi + r0[i]);
+    const double ui = A.given_up ? u[i] : fma(-piq[last], p, A.inv_Q[last] * bu[i]);
     const double lo_y = A.ya ? A.ya[i] : A.ya_s, hi_y = A.yb ? A.yb[i] : A.yb_s;
     const double lo_u = A.ua ? A.ua[i] : A.ua_s, hi_u = A.ub ? A.ub[i] : A.ub_s;
-    const double zy = fmin(fmax(yi + A.delta * A.wy[i], lo_y), hi_y);
-    const double zu = fmin(fmax(ui + A.delta_over_psi * A.wu[i], lo_u), hi_u);
-    A.wy[i] += A.rho_over_delta * (yi - zy);
-    A.wu[i] += A.rho_over_delta * A.psi * (ui - zu);
+    const double zy = fmin(fmax(fma(A.delta, A.wy[i], yi), lo_y), hi_y);
+    const double zu = fmin(fmax(fma(A.delta_over_psi, A.wu[i], ui), lo_u), hi_u);
+    const double dy = yi - zy, du = ui - zu;
+    A.wy[i] = fma(A.rho_over_delta, dy, A.wy[i]);
+    A.wu[i] = fma(rpsi, du, A.wu[i]);
     A.zy[i] = zy;
     A.zu[i] = zu;
     A.p[i] = p;
     u[i] = ui;
-    const double gi = A.g ? A.g[i] : 0.0;
-    const double e = fabs(byi + A.psi * (ui - gi));
-    const double dy = fabs(yi - zy), du = fabs(ui - zu);
-    bad |= !isfinite(e) || !isfinite(dy) || !isfinite(du);
-    m_eq = fmax(m_eq, e);
-    m_y = fmax(m_y, dy);
-    m_u = fmax(m_u, du);
+    const double e = A.g ? fma(A.psi, ui - A.g[i], byi) : fma(A.psi, ui, byi);
+    m_eq = max(m_eq, abs_bits(e));
+    m_y = max(m_y, abs_bits(dy));
+    m_u = max(m_u, abs_bits(du));
     const double dd = yi - A.ybar[i];
-    obj += 0.5 * w * dd * dd + 0.5 * A.gamma * w * ui * ui;
+    if (last) {
+      oyl = fma(dd, dd, oyl);
+      oul = fma(ui, ui, oul);
+    } else {
+      oy = fma(dd, dd, oy);
+      ou = fma(ui, ui, ou);
+    }
   }
-  m_eq = block_max(m_eq, sh);
-  m_y = block_max(m_y, sh);
-  m_u = block_max(m_u, sh);
+  // objective 1/2 (y - ybar)^T J1 (y - ybar) + 1/2 u^T J2 u with J1 = diag(w), J2 = gamma J1
+  double obj = 0.5 * (A.w[0] * fma(A.gamma, ou, oy) + A.w[1] * fma(A.gamma, oul, oyl));
+  m_eq = block_max_bits(m_eq, shl);
+  m_y = block_max_bits(m_y, shl);
+  m_u = block_max_bits(m_u, shl);
   obj = block_sum(obj, sh);
-  const double flag = block_max(bad ? 1.0 : 0.0, sh);
   if (threadIdx.x == 0) {
-    partials[blockIdx.x] = m_eq;
-    partials[np + blockIdx.x] = m_y;
-    partials[2 * np + blockIdx.x] = m_u;
+    const long long inf_bits = 0x7ff0000000000000LL;
+    const bool bad = m_eq >= inf_bits || m_y >= inf_bits || m_u >= inf_bits || !isfinite(obj);
+    partials[blockIdx.x] = bad ? 0.0 : __longlong_as_double(m_eq);
+    partials[np + blockIdx.x] = bad ? 0.0 : __longlong_as_double(m_y);
+    partials[2 * np + blockIdx.x] = bad ? 0.0 : __longlong_as_double(m_u);
     partials[3 * np + blockIdx.x] = obj;
-    partials[4 * np + blockIdx.x] = flag;
+    partials[4 * np + blockIdx.x] = bad ? 1.0 : 0.0;
   }
 }
 
