@@ -408,16 +408,21 @@ def run_ours(args):
         hy.copy_(torch.as_tensor(inst.ybar.ravel()))
         hout_y = torch.empty(N, dtype=torch.float64, pin_memory=True)
         hout_u = torch.empty(N, dtype=torch.float64, pin_memory=True)
-        torch.cuda.synchronize()
-        a.record(st)
-        for _ in range(max(1, args.steps // 2)):
+        def e2e_step():
             ybar.copy_(hy, non_blocking=True)
             rr = step()
             hout_y.copy_(rr["y"], non_blocking=True)
             hout_u.copy_(rr["u"], non_blocking=True)
+
+        e2e_step()  # warm-up: first touch of the host buffers by the copy engines
+        torch.cuda.synchronize()
+        n_e2e = max(2, args.steps)
+        a.record(st)
+        for _ in range(n_e2e):
+            e2e_step()
         b.record(st)
         torch.cuda.synchronize()
-        te = a.elapsed_time(b) / 1e3 / max(1, args.steps // 2)
+        te = a.elapsed_time(b) / 1e3 / n_e2e
         extras["e2e"] = {"value": te, "unit": "s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 16 * N}
         if rank == 0:
             extras["cpu_baseline"] = cpu_baseline(inst, stats["pcg_iters"] + stats["fp64_matvecs"] / 2)

@@ -132,7 +132,8 @@ typedef struct fde_admm_stats {
   int admm_iters;            /* iterations performed                                             */
   int pcg_iters;             /* PCG iterations summed over all sub-problems                      */
   int refine_steps;          /* MIXED: refinement corrections summed over sub-problems           */
-  int fp64_matvecs;          /* double-precision B or B^T applications                           */
+  int fp64_matvecs;          /* B or B^T applications on double vectors (double or, in the
+                                MIXED_DF / MIXED_DFV refinement, double-float arithmetic)        */
   double res_eq;             /* ||B y + psi (u - g)||_inf at exit                                */
   double res_y;              /* ||y - z_y||_inf at exit                                          */
   double res_u;              /* ||u - z_u||_inf at exit                                          */
