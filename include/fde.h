@@ -126,6 +126,10 @@ typedef struct fde_admm_opts {
                                 preconditioner, Section 3.2.2) with D-tilde = C3: D-hat = C3^T +
                                 sqrt(m1 m2) I is circulant, so S-hat is applied by the same FFTs
                                 with sigma = m1 + |Lambda|^2/m2 + 2 sqrt(m1/m2) Re(Lambda).         */
+  int warm_start;            /* 1: fde_admm_solve starts from the iterates (y, u, z_y, z_u, p, w_y,
+                                w_u) the previous fde_admm_solve on this problem ended with, instead
+                                of zero (FDE_EINVAL if there is none); the options and the data
+                                may differ between the calls. Batches: FDE_EUNSUPPORTED.          */
 } fde_admm_opts;
 
 typedef struct fde_admm_stats {
@@ -219,7 +223,8 @@ int fde_precond(fde_problem* prob, const fde_admm_opts* opts, int precision,
  * (NULL = unbounded on that side). Scalar bounds are passed as
  * ya_s/yb_s/ua_s/ub_s and are used where the matching array pointer is NULL;
  * give -INFINITY/+INFINITY for no bound. Outputs (double, device, length N):
- * y, u (required), p, z_u (NULL = not returned). Iterates start at zero.
+ * y, u (required), p, z_u (NULL = not returned). Iterates start at zero, or
+ * with opts->warm_start where the previous solve on `prob` ended.
  * stats may be NULL. Errors: FDE_EINVAL, FDE_ENOCONV (cap reached: outputs
  * and stats hold the last iterate), FDE_EBREAKDOWN, FDE_ENONFINITE,
  * FDE_ECUDA. Synchronises `stream`. */

@@ -148,6 +148,7 @@ bool valid_opts(const fde_admm_opts* o) {
   if (o->algorithm < 0 || o->algorithm > 2) return false;
   if (o->inner_solver < 0 || o->inner_solver > 1) return false;
   if (o->precond < 0 || o->precond > 1) return false;
+  if (o->warm_start < 0 || o->warm_start > 1) return false;
   if (generalized(o)) return o->rho <= 1.0 && std::isfinite(o->c_y) && o->c_y >= 1.0 && std::isfinite(o->c_u);
   return true;
 }
@@ -783,8 +784,14 @@ int fde_admm_solve(fde_problem* P, const fde_admm_opts* o, const double* ybar, c
   AdmmArgs A = make_admm_args(P, o, dg, ybar, g, ya, yb, ua, ub, ya_s, yb_s, ua_s, ub_s);
   double* Y = P->v64[V_Y];
   double* U = P->v64[V_U];
-  // zero iterates; V_BY = B y = 0 holds the invariant "V_BY = B Y" kept across iterations
-  for (int i : {V_Y, V_U, V_ZY, V_ZU, V_P, V_WY, V_WU, V_BY}) CK(fill<double>(P->v64[i], 0.0, N, st));
+  // zero iterates, or (warm start) the iterates the previous solve ended with; V_BY = B Y
+  // holds in both cases (B 0 = 0; a solve leaves B of its final y) and is kept across iterations
+  if (o->warm_start) {
+    if (!P->state_valid) return FDE_EINVAL;
+  } else {
+    for (int i : {V_Y, V_U, V_ZY, V_ZU, V_P, V_WY, V_WU, V_BY}) CK(fill<double>(P->v64[i], 0.0, N, st));
+  }
+  P->state_valid = false;  // set again once this solve has left a consistent state
 
   fde_admm_stats S{};
   SolveInfo info;
@@ -884,6 +891,7 @@ int fde_admm_solve(fde_problem* P, const fde_admm_opts* o, const double* ybar, c
   if (zu) CK(cudaMemcpyAsync(zu, A.zu, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
   CK(cudaStreamSynchronize(st));
   if (stats) *stats = S;
+  P->state_valid = status == FDE_OK || status == FDE_ENOCONV;
   return status;
 }
 
@@ -898,7 +906,7 @@ int fde_admm_grad(fde_problem* P, const double* y, const double* ybar, const dou
   const double w1 = P->prm.weights == 0 ? 0.5 : 1.0;
   double* f = P->v64[V_C];
   double* rhs = P->v64[V_RHS];
-  double* pv = P->v64[V_P];
+  double* pv = P->v64[V_BU];  // not V_P: the ADMM iterates stay intact (warm start)
   auto s = scratch64(P);
   // f = -J1 (y - ybar) - w_y
   CK(grad_ybar(y, ybar, wy, 1.0, w1, (long long)(P->nt - 1) * P->nx * P->ny, N, dJ_dybar, f, st));
@@ -1145,6 +1153,7 @@ int fde_batch_admm_solve(fde_batch* b, const fde_admm_opts* o, const double* con
   for (int i = 0; i < n; ++i)
     if (!valid_opts_for(b->probs[i], o)) return FDE_EINVAL;
   if (o->inner_solver != 0) return FDE_EUNSUPPORTED;  // the graph solve runs PCG only
+  if (o->warm_start) return FDE_EUNSUPPORTED;         // a replayed graph starts from zero
   bool same = b->exec && std::memcmp(&b->opts, o, sizeof(*o)) == 0;
   for (int i = 0; i < n; ++i) {
     if (!ybar[i] || !y[i] || !u[i]) return FDE_EINVAL;

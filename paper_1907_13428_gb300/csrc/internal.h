@@ -81,6 +81,7 @@ struct fde_problem {
   // tile choice of the double-float passes: 256 (both halves per thread) or split (-256/-512 x2, -512 x1)
   int rows_ntdd = 256;
   int axis_ntdd = 256;
+  bool state_valid = false;  // the ADMM iterates hold the end of a previous solve (warm start)
 };
 
 namespace fde {

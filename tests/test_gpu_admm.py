@@ -214,3 +214,31 @@ def test_gradient_differentiation_workload_full_size_properties():
     assert np.all(np.isfinite(coef.numpy()))
     prob.close()
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec_name,inner_solver", [("FDE_FP64", 0), ("FDE_MIXED_DFV", 0), ("FDE_FP64", 1)])
+def test_warm_start_continues_the_iteration(prec_name, inner_solver):
+    """K1 iterations, then K2 more with warm_start, equal K1 + K2 iterations in one
+    solve; without a previous solve a warm start is rejected."""
+    need_gpu()
+    F = lib()
+    inst = _instance(16, 12, 6, ua=-0.05, ub=0.05, yb=0.3)
+    prec = getattr(F, prec_name)
+    base = dict(delta=0.8, rho=1.618, fixed_iters=True, inner_tol_mode=1, inner_tol=1e-12, precision=prec,
+                inner_solver=inner_solver, max_pcg=3000)
+    prob = F.Problem(inst.params)
+    kw = dict(g=dev(inst.g), ya=inst.ya, yb=inst.yb, ua=inst.ua, ub=inst.ub, allow_noconv=True)
+    with pytest.raises(F.FdeError) as e:
+        prob.admm_solve(F.AdmmOptions(**base, max_admm=2, warm_start=True), dev(inst.ybar), **kw)
+    assert e.value.status == F.FDE_EINVAL
+    one = prob.admm_solve(F.AdmmOptions(**base, max_admm=7), dev(inst.ybar), **kw)
+    y7 = host(one["y"])
+    first = prob.admm_solve(F.AdmmOptions(**base, max_admm=3), dev(inst.ybar), **kw)
+    # other calls on the problem in between leave the iterates alone
+    prob.admm_grad(first["y"], dev(inst.ybar))
+    prob.matvec(dev(inst.ybar), F.FDE_OP_S, F.AdmmOptions(**base))
+    two = prob.admm_solve(F.AdmmOptions(**base, max_admm=4, warm_start=True), dev(inst.ybar), **kw)
+    assert relerr(host(two["y"]), y7) < 1e-9
+    ref = O.admm_direct(inst, O.AdmmOptions(delta=0.8, rho=1.618), iters=7)
+    assert relerr(host(two["y"]), ref.y) < 1e-8
+    prob.close()

@@ -226,3 +226,26 @@ def test_set_tiles_rejects_unknown_values():
             prob.set_tiles(*bad)
         assert e.value.status == F.FDE_EINVAL
     prob.close()
+
+
+@pytest.mark.parametrize("dims,alpha", [((4096, 3, 2), 1.0), ((2, 4096, 2), 1.0), ((3, 5, 4096), 0.6),
+                                        ((2, 4095, 3), 1.0)])
+def test_largest_axis_length(dims, alpha):
+    """Axes of the largest supported length (4096: the 4096-point register FFT,
+    three radix-16/16/16 passes) and a ragged 4095, in double, float and
+    double-float (every double-float tile), against the oracle."""
+    need_gpu()
+    F = lib()
+    nx, ny, nt = dims
+    p = params(nx, ny, nt, alpha_t=alpha)
+    prob = F.Problem(p)
+    x = fi.random_field(53, (nt, nx, ny))
+    xd = dev(x)
+    for op, tr in ((F.FDE_OP_B, False), (F.FDE_OP_BT, True)):
+        ref = O.apply_B(p, x, transpose=tr)
+        assert relerr(host(prob.matvec(xd, op)), ref) < 1e-12
+        assert relerr(host(prob.matvec(xd.float(), op)), ref) < 5e-5
+        for rows, axis in ((256, 256), (-512, -512)):
+            prob.set_tiles(rows, axis, dfloat=True)
+            assert relerr(host(prob.matvec(xd, op, dfloat=True)), ref) < 1e-11, (rows, axis)
+    prob.close()
