@@ -299,6 +299,7 @@ def run_ours(args):
         d2h_ms = sum(m[1].elapsed_time(m[2]) for m in marks) / n_e2e
         extras["e2e"] = {"value": te, "unit": "s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 16 * N,
                          "steps": n_e2e, "solve_ms_in_e2e": solve_ms, "d2h_ms": d2h_ms,
+                         "h2d_ms": te * 1e3 - solve_ms - d2h_ms,
                          "host_buffers_pinned": bool(hy.is_pinned() and hout_y.is_pinned() and hout_u.is_pinned()),
                          "clocks": eclk.summary()}
         # Toeplitz-FFT matvec (float, y = B x) and the other operator units, timed alone
