@@ -143,6 +143,8 @@ typedef struct fde_admm_stats {
   double res_u;              /* ||u - z_u||_inf at exit                                          */
   double objective;          /* 1/2 (y-ybar)^T J1 (y-ybar) + 1/2 u^T J2 u at exit                */
   double max_sub_relres;     /* largest final relative residual ||b - S y||/||b|| of a sub-solve */
+  int recursive_steers;      /* MIXED_DFV: corrections steered by the float PCG's recursive
+                                residual instead of an evaluated one                              */
 } fde_admm_stats;
 
 typedef struct fde_problem fde_problem;

@@ -43,7 +43,8 @@ class fde_admm_opts(ctypes.Structure):
 class fde_admm_stats(ctypes.Structure):
     _fields_ = [("admm_iters", ctypes.c_int), ("pcg_iters", ctypes.c_int), ("refine_steps", ctypes.c_int),
                 ("fp64_matvecs", ctypes.c_int), ("res_eq", ctypes.c_double), ("res_y", ctypes.c_double),
-                ("res_u", ctypes.c_double), ("objective", ctypes.c_double), ("max_sub_relres", ctypes.c_double)]
+                ("res_u", ctypes.c_double), ("objective", ctypes.c_double), ("max_sub_relres", ctypes.c_double),
+                ("recursive_steers", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -259,7 +259,7 @@ int op_M(fde_problem* P, const Diags& dg, const R* r, R* z, cudaStream_t st, Gat
 }
 
 struct SolveInfo {
-  int pcg_iters = 0, refine = 0, fp64_matvecs = 0;
+  int pcg_iters = 0, refine = 0, fp64_matvecs = 0, recursive = 0;
   double relres = 0.0;
 };
 
@@ -314,32 +314,52 @@ int subsolve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const doub
   const bool dfv = o->precision == FDE_MIXED_DFV;
   bool dd = o->precision == FDE_MIXED_DF || dfv;
   bool by_dd = o->precision == FDE_MIXED_DF;  // V_BY holds a double-float product
+  // FDE_MIXED_DFV also lets the float PCG's recursive residual r - S d steer the next
+  // correction when it is accurate enough: its error, rounding drift plus the float operator's
+  // own error, is about kFloatDrift of the residual the correction started from, so a start
+  // residual rel with rel * kFloatDrift <= tol / 10 skips one evaluation (two products).
+  constexpr double kFloatDrift = 1e-6;
+  bool implicit_next = false;
+  double rel_implicit = 0.0;
   for (int k = 0; k <= maxref; ++k) {
     double rel = 0.0;
-    // on entry V_BY already holds B y for the warm start (kept by the ADMM loop)
-    const bool y_changed = k > 0 || !by_on_entry;
-    for (int pass = 0; pass < 2; ++pass) {
-      if ((pass == 0 && y_changed) || (by_dd && !dd)) {
-        CK(refine_B(P, dd, 0, y, P->v64[V_BY], nullptr, nullptr, s64.t1, s64.t2, st));
+    const bool had_implicit = implicit_next;
+    implicit_next = false;
+    const bool implicit = had_implicit && rel_implicit > tol && k < maxref;
+    if (implicit) {
+      rel = rel_implicit;
+      CK(copy<float>(P->v32[F_B], P->v32[F_R], N, st));  // the recursive residual is the next right-hand side
+      dd = rel * inner > tol;
+      info->recursive += 1;
+    } else {
+      // the recursive residual already meets tol (or this is the last evaluation): verify in double
+      if (had_implicit) dd = false;
+      // on entry V_BY already holds B y for the warm start (kept by the ADMM loop)
+      const bool y_changed = k > 0 || !by_on_entry;
+      for (int pass = 0; pass < 2; ++pass) {
+        if ((pass == 0 && y_changed) || (by_dd && !dd)) {
+          CK(refine_B(P, dd, 0, y, P->v64[V_BY], nullptr, nullptr, s64.t1, s64.t2, st));
+          info->fp64_matvecs += 1;
+          by_dd = dd;
+        }
+        CK(fold(P->v64[V_BY], q, c, y, dg.M2inv.v, dg.M1.v, last, N, P->v64[V_SD], P->v64[V_Z], st));
+        CK(refine_B(P, dd, 1, P->v64[V_SD], P->v64[V_R], P->v64[V_Z], &one, s64.t1, s64.t2, st));
         info->fp64_matvecs += 1;
-        by_dd = dd;
+        *by_valid = !by_dd || o->precision == FDE_MIXED_DF;
+        CK((dot<double, double>(P, P->v64[V_R], P->v64[V_R], N, S_RR, FIN_STORE, st)));
+        flag = read_scalars(P, st);
+        if (flag < 0) return flag;
+        rel = std::sqrt(P->hscal[S_RR] / bb);
+        if (!(dfv && dd && rel <= tol)) break;
+        dd = false;  // met tol in double-float: evaluate again in double
       }
-      CK(fold(P->v64[V_BY], q, c, y, dg.M2inv.v, dg.M1.v, last, N, P->v64[V_SD], P->v64[V_Z], st));
-      CK(refine_B(P, dd, 1, P->v64[V_SD], P->v64[V_R], P->v64[V_Z], &one, s64.t1, s64.t2, st));
-      info->fp64_matvecs += 1;
-      *by_valid = !by_dd || o->precision == FDE_MIXED_DF;
-      CK((dot<double, double>(P, P->v64[V_R], P->v64[V_R], N, S_RR, FIN_STORE, st)));
-      flag = read_scalars(P, st);
-      if (flag < 0) return flag;
-      rel = std::sqrt(P->hscal[S_RR] / bb);
-      if (!(dfv && dd && rel <= tol)) break;
-      dd = false;  // met tol in double-float: evaluate again in double
+      rel_implicit = 0.0;
+      info->relres = rel;
+      if (rel <= tol) return FDE_OK;
+      if (k == maxref) break;
+      if (dfv) dd = rel * inner > tol;
+      CK(to_f32(P->v64[V_R], P->v32[F_B], N, st));
     }
-    info->relres = rel;
-    if (rel <= tol) return FDE_OK;
-    if (k == maxref) break;
-    if (dfv) dd = rel * inner > tol;
-    CK(to_f32(P->v64[V_R], P->v32[F_B], N, st));
     int it = 0;
     double rr32 = 0;
     // the float correction only needs to reduce the residual by `inner`
@@ -350,6 +370,10 @@ int subsolve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const doub
     if (s != FDE_OK && s != FDE_ENOCONV) return s;
     CK(add_f32(y, P->v32[F_X], N, st));
     *by_valid = false;
+    if (dfv && !implicit && rel * kFloatDrift <= 0.1 * tol) {
+      implicit_next = true;
+      rel_implicit = rr32 * rel;  // |r - S d| / |rhs| from the PCG's own residual
+    }
   }
   return FDE_ENOCONV;
 }
@@ -881,6 +905,7 @@ int fde_admm_solve(fde_problem* P, const fde_admm_opts* o, const double* ybar, c
   }
   S.pcg_iters = info.pcg_iters;
   S.refine_steps = info.refine;
+  S.recursive_steers = info.recursive;
   S.fp64_matvecs = info.fp64_matvecs;
   S.res_eq = res[0];
   S.res_y = res[1];

@@ -280,3 +280,23 @@ def test_dfv_full_size_against_mixed_and_fp64():
     del ys
     prob.close()
     torch.cuda.empty_cache()
+
+
+def test_dfv_recursive_steering_in_a_converged_run():
+    """A long FDE_MIXED_DFV run: once the warm starts are good, corrections are
+    steered by the float PCG's recursive residual (counted in the stats); every
+    accepted sub-problem residual is still a double evaluation below its target,
+    and the run reaches the polished KKT point."""
+    need_gpu()
+    F = lib()
+    inst = _instance(8, 6, 5, ua=-0.05, ub=0.05)
+    sol = O.polish(inst, O.admm_direct(inst, O.AdmmOptions(delta=1.0, rho=1.618, tol=1e-11, max_iter=20000)))
+    prob = F.Problem(inst.params)
+    fo = F.AdmmOptions(delta=1.0, rho=1.618, tol_admm=1e-8, max_admm=20000, inner_tol_mode=1, inner_tol=1e-8,
+                       precision=F.FDE_MIXED_DFV, inner_tol_mixed=1e-4)
+    r = prob.admm_solve(fo, dev(inst.ybar), g=dev(inst.g), ua=inst.ua, ub=inst.ub)
+    prob.close()
+    s = r["stats"]
+    assert s["recursive_steers"] > 0, s
+    assert s["max_sub_relres"] <= 1e-8
+    assert relerr(host(r["y"]), sol.y) < 1e-6 and relerr(host(r["u"]), sol.u) < 1e-6
