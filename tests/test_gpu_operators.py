@@ -249,3 +249,29 @@ def test_largest_axis_length(dims, alpha):
             prob.set_tiles(rows, axis, dfloat=True)
             assert relerr(host(prob.matvec(xd, op, dfloat=True)), ref) < 1e-11, (rows, axis)
     prob.close()
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_preconditioner_full_size_properties(precond):
+    """1024^2 x 128 (the benchmark's grid): S-tilde^-1 (and the matching S-hat^-1)
+    is symmetric and positive definite, <M x, w> = <x, M w> and <M x, x> > 0, and the
+    float application agrees with the double one."""
+    need_gpu()
+    F = lib()
+    inst = fi.config_large()
+    prob = F.Problem(inst.params)
+    fo = F.AdmmOptions(delta=1.0, rho=1.618, precond=precond)
+    x = dev(inst.ybar)
+    w = dev(fi.random_field(61, prob.shape))
+    mx = prob.precond(x, fo)
+    mw = prob.precond(w, fo)
+    a = float(torch.dot(mx, w))
+    b = float(torch.dot(x, mw))
+    assert abs(a - b) <= 1e-10 * max(abs(a), abs(b)), (a, b)
+    assert float(torch.dot(mx, x)) > 0 and float(torch.dot(mw, w)) > 0
+    m32 = prob.precond(x.float(), fo)
+    scale = float(mx.abs().max())
+    assert float((m32.double() - mx).abs().max()) / scale < 1e-4
+    del mx, mw, m32, x, w
+    prob.close()
+    torch.cuda.empty_cache()
