@@ -1,9 +1,9 @@
 // Double-float arithmetic: a value is the unevaluated sum hi + lo of two
-// floats with |lo| <= ulp(hi)/2, about 48 significand bits. Error-free
-// transformations after Knuth (TwoSum), Dekker (Fast2Sum) and the fused
-// multiply-add product error (TwoProd); addition is the "sloppy" double-float
-// sum (relative error about 2^-44 of |a| + |b|), multiplication keeps the
-// cross terms hi*lo (relative error about 2^-46).
+// floats, about 48 significand bits. Error-free transformations after Knuth
+// (TwoSum), Dekker (Fast2Sum) and the fused multiply-add product error
+// (TwoProd); addition is the "sloppy" double-float sum without renormalisation
+// (error about 2^-46 of |a| + |b|), multiplication keeps the cross terms hi*lo
+// and renormalises (relative error about 2^-46).
 //
 // Used for the refinement residual of the mixed solve (FDE_MIXED_DF): GB300
 // runs float arithmetic 58 times faster than double, and a double-float
@@ -25,11 +25,16 @@ __device__ __forceinline__ dd dd_fast2sum(float a, float b) {
   return dd(s, b - (s - a));
 }
 
+// Sum without the final renormalisation: hi is the float sum of the high parts,
+// lo collects its exact rounding error (TwoSum) and the low parts. The pair is
+// an unevaluated sum whose lo may exceed half an ulp of hi; products renormalise
+// (operator*), and in the transforms every product has one normalised factor (a
+// twiddle or a symbol value), so the norm-wise error stays near 2^-46.
 __device__ __forceinline__ dd operator+(dd a, dd b) {
   const float s = a.hi + b.hi;
   const float bb = s - a.hi;
   const float e = (a.hi - (s - bb)) + (b.hi - bb);
-  return dd_fast2sum(s, e + a.lo + b.lo);
+  return dd(s, e + (a.lo + b.lo));
 }
 
 __host__ __device__ constexpr dd operator-(dd a) { return dd(-a.hi, -a.lo); }
