@@ -467,7 +467,8 @@ namespace fde {
 // line-major with one pad element per 16 (conflict-free exchanges).
 // R: arithmetic of the transforms; S: storage type of the vectors (R, or double
 // for double-float arithmetic).
-template <typename R, int L, int NT, typename S = R>
+// FULL: the lines fill the transform (n == L), so no position is out of range.
+template <typename R, int L, int NT, typename S = R, bool FULL = false>
 __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const S* __restrict__ x, long long nrows,
                                                   int n, const cplx<R>* __restrict__ sym,
                                                   const cplx<R>* __restrict__ tw2, const cplx<R>* __restrict__ twL,
@@ -486,12 +487,12 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const
   for (int r = 0; r < 16; ++r) {
     const int p = t + r * T;
     R a = 0, b = 0;
-    if (p < n) {
+    if (FULL || p < n) {
       if (ra < nrows) a = cvt_in<R, S>(x[ra * n + p]);
       if (rb < nrows) b = cvt_in<R, S>(x[rb * n + p]);
     }
     v[0][r] = mk<C>(a, b);
-    v[1][r] = p < n ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
+    v[1][r] = (FULL || p < n) ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
   }
   rf_forward<R, L, 2>(v, t, twL, at);
 #pragma unroll
@@ -514,14 +515,14 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int p = t + (r0 + k) * T;
-      const bool ok = p < n;
+      const bool ok = FULL || p < n;
       ia[k] = (ok && ra < nrows) ? epi_load(E, ra * n + p, ta) : EpiIn<S>{0, 0, 0, 0};
       ib[k] = (ok && rb < nrows) ? epi_load(E, rb * n + p, tb) : EpiIn<S>{0, 0, 0, 0};
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int p = t + (r0 + k) * T;
-      if (p < n) {
+      if (FULL || p < n) {
         const C res = cadd(v[0][r0 + k], cmul(v[1][r0 + k], cconj(ldg_(&tw2[p]))));
         if (ra < nrows) epi_finish(E, ia[k], ra * n + p, ta, cvt_out<S, R>(res.x));
         if (rb < nrows) epi_finish(E, ib[k], rb * n + p, tb, cvt_out<S, R>(res.y));
@@ -535,7 +536,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const
 // halves' lines side by side; the line index is XOR-swizzled by the parity of
 // the low five position bits, which separates the two position groups of every
 // half-warp into different banks.
-template <typename R, int L, int NT, typename S = R>
+template <typename R, int L, int NT, typename S = R, bool FULL = false>
 __global__ void __launch_bounds__(NT) k_axis_reg(const S* __restrict__ x, int n, long long axis_stride,
                                                   long long n_inner, long long outer_stride, long long n_outer,
                                                   const cplx<R>* __restrict__ sym, const cplx<R>* __restrict__ tw2,
@@ -564,7 +565,7 @@ __global__ void __launch_bounds__(NT) k_axis_reg(const S* __restrict__ x, int n,
   for (int r = 0; r < 16; ++r) {
     const int p = t + r * T;
     R a = 0, b = 0;
-    if (valid && p < n) {
+    if (valid && (FULL || p < n)) {
       const long long idx = base + p * axis_stride;
       if (vec2 && has_b) {
         const cplx<S> ab = *reinterpret_cast<const cplx<S>*>(x + idx);  // (c, c+1) as one aligned vector load
@@ -576,7 +577,7 @@ __global__ void __launch_bounds__(NT) k_axis_reg(const S* __restrict__ x, int n,
       }
     }
     v[0][r] = mk<C>(a, b);
-    v[1][r] = p < n ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
+    v[1][r] = (FULL || p < n) ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
   }
   rf_forward<R, L, 2>(v, t, twL, at);
 #pragma unroll
@@ -593,7 +594,7 @@ __global__ void __launch_bounds__(NT) k_axis_reg(const S* __restrict__ x, int n,
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
     const int p = t + r * T;
-    if (valid && p < n) {
+    if (valid && (FULL || p < n)) {
       const C res = cadd(v[0][r], cmul(v[1][r], cconj(ldg_(&tw2[p]))));
       const long long idx = base + p * axis_stride;
       if (E.plain && vec2 && has_b) {
@@ -787,6 +788,13 @@ static cudaError_t launch_rows_reg_LN(fde_problem* P, const S* x, int conj_sym, 
   const long long npairs = (nrows + 1) / 2;
   const long long grid = (npairs + PAIRS - 1) / PAIRS;
   const size_t smem = (size_t)PAIRS * 2 * (L + L / 16) * sizeof(cplx<R>);
+  if constexpr (std::is_same<R, float>::value) {
+    if (P->ax[2].n == L) {
+      k_rows_reg<R, L, NT, S, true><<<(unsigned)grid, NT, smem, st>>>(x, nrows, L, sym, T.tw2, T.twL, conj_sym, E);
+      note_launches(1);
+      return cudaGetLastError();
+    }
+  }
   k_rows_reg<R, L, NT, S><<<(unsigned)grid, NT, smem, st>>>(x, nrows, P->ax[2].n, sym, T.tw2, T.twL, conj_sym, E);
   note_launches(1);
   return cudaGetLastError();
@@ -836,6 +844,14 @@ static cudaError_t launch_axis_reg_LN(const S* x, int n, long long axis_stride, 
   const size_t al = 2 * sizeof(S);
   const int vec2 = ((n_inner | axis_stride | outer_stride) & 1) == 0 && ((uintptr_t)x % al) == 0 &&
                    ((uintptr_t)E.out % al) == 0;
+  if constexpr (std::is_same<R, float>::value) {
+    if (n == L) {
+      k_axis_reg<R, L, NT, S, true><<<(unsigned)grid, NT, smem, st>>>(x, L, axis_stride, n_inner, outer_stride,
+                                                                      n_outer, sym, T.tw2, T.twL, conj_sym, E, vec2);
+      note_launches(1);
+      return cudaGetLastError();
+    }
+  }
   k_axis_reg<R, L, NT, S><<<(unsigned)grid, NT, smem, st>>>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym,
                                                             T.tw2, T.twL, conj_sym, E, vec2);
   note_launches(1);
@@ -970,6 +986,25 @@ cudaError_t toeplitz_reg_set_smem_attrs() {
     e = cudaFuncSetAttribute(k_axis_reg<float, LL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   FDE_FOR_EACH_L(FDE_ATTR2)
 #undef FDE_ATTR2
+#define FDE_ATTR9(LL)                                                                                        \
+  if (e == cudaSuccess)                                                                                      \
+    e = cudaFuncSetAttribute(k_rows_reg<float, LL, 256, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             big);                                                                           \
+  if (e == cudaSuccess)                                                                                      \
+    e = cudaFuncSetAttribute(k_axis_reg<float, LL, 512, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             big);                                                                           \
+  if (e == cudaSuccess)                                                                                      \
+    e = cudaFuncSetAttribute(k_axis_reg<float, LL, 256, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             big);
+  FDE_FOR_EACH_L(FDE_ATTR9)
+#undef FDE_ATTR9
+#define FDE_ATTR10(LL)                                                                                       \
+  if (e == cudaSuccess)                                                                                      \
+    e = cudaFuncSetAttribute(k_rows_reg<float, LL, 128, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             big);
+  FDE_ATTR10(16) FDE_ATTR10(32) FDE_ATTR10(64) FDE_ATTR10(128) FDE_ATTR10(256) FDE_ATTR10(512) FDE_ATTR10(1024)
+  FDE_ATTR10(2048)
+#undef FDE_ATTR10
 #define FDE_ATTR3(LL)                                                                                        \
   if (e == cudaSuccess)                                                                                      \
     e = cudaFuncSetAttribute(k_rows_reg<float, LL, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);

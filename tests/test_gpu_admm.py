@@ -242,3 +242,37 @@ def test_warm_start_continues_the_iteration(prec_name, inner_solver):
     ref = O.admm_direct(inst, O.AdmmOptions(delta=0.8, rho=1.618), iters=7)
     assert relerr(host(two["y"]), ref.y) < 1e-8
     prob.close()
+
+
+@pytest.mark.parametrize("prec_name,inner_solver", [("FDE_FP64", 0), ("FDE_MIXED", 0), ("FDE_MIXED_DFV", 0),
+                                                    ("FDE_FP64", 1), ("FDE_MIXED_DFV", 1)])
+def test_zero_data_gives_zero_solution(prec_name, inner_solver):
+    """ybar = 0, g = 0 and no bounds: every right-hand side vanishes and the iterates
+    stay exactly zero (the zero-norm branches of the sub-solves)."""
+    need_gpu()
+    F = lib()
+    p = params(12, 10, 4)
+    prob = F.Problem(p)
+    fo = F.AdmmOptions(delta=1.0, rho=1.618, max_admm=3, fixed_iters=True, inner_tol_mode=1, inner_tol=1e-10,
+                       precision=getattr(F, prec_name), inner_solver=inner_solver, max_pcg=500)
+    r = prob.admm_solve(fo, dev(np.zeros(prob.N)), allow_noconv=True)
+    for k in ("y", "u", "p", "zu"):
+        assert float(r[k].abs().max()) == 0.0, k
+    assert r["stats"]["objective"] == 0.0
+    prob.close()
+
+
+def test_coincident_bounds_fix_the_control():
+    """u_a = u_b: the projected copy z_u is that value everywhere and the iterates
+    match the oracle's (FP64, fixed iterations)."""
+    need_gpu()
+    F = lib()
+    inst = _instance(10, 8, 4, ua=0.01, ub=0.01)
+    K = 8
+    ref = O.admm_direct(inst, O.AdmmOptions(delta=0.8, rho=1.618), iters=K)
+    fo = F.AdmmOptions(delta=0.8, rho=1.618, max_admm=K, fixed_iters=True, inner_tol_mode=1, inner_tol=1e-13,
+                       precision=F.FDE_FP64)
+    r = _run(F, inst, fo)
+    assert float((r["zu"] - 0.01).abs().max()) == 0.0
+    for k in ("y", "u", "p"):
+        assert relerr(host(r[k]), getattr(ref, k)) < 1e-10, k
