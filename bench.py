@@ -222,7 +222,8 @@ def run_ours(args):
     inst = workload(args.workload)
     p = inst.params
     prob = F.Problem(p)
-    tiles = {"float": prob.autotune(), "dfloat": prob.tiles(dfloat=True)}  # FFT tiles timed on this problem
+    # FFT tiles timed on this problem
+    tiles = {"float": prob.autotune(), "dfloat": prob.tiles(dfloat=True), "fp64": prob.tiles(fp64=True)}
     N = prob.N
     ybar = torch.as_tensor(inst.ybar.ravel(), device=dev)
     bounds = dict(ya=inst.ya, yb=inst.yb, ua=inst.ua, ub=inst.ub)
@@ -343,25 +344,31 @@ def run_ours(args):
         while L < p.ny:
             L *= 2
         flops = (10.0 * math.log2(L) + 13.0) * N
-        # dominant kernel of the solve (launch-list share): the float x2 Toeplitz pass of the
-        # PCG operator. Its arithmetic roof (flops at the measured float FMA rate) lies above
-        # its memory roof (8N bytes at the measured copy bandwidth), so it is reported as ALU-bound.
+        # dominant kernel of the solve (launch-list share): the double x2 Toeplitz pass of the
+        # verifying residual evaluations, bound by the double pipe (its flops at the measured
+        # double FMA rate take about 40x longer than its 16N bytes at the measured copy rate)
+        achieved = flops / (t_x2_64 * 1e-3) / 1e12
+        gbs64 = 16.0 * N / (t_x2_64 * 1e-3) / 1e9
+        extras["roofline"] = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                              "frac": achieved / fp64_peak, "traffic": traffic_for("k_rows_reg_double_1024"),
+                              "kernel": "k_rows_reg<double,1024>: x2 Toeplitz pass in double (one launch)",
+                              "flops_per_launch": flops, "ms": t_x2_64,
+                              "peak_source": "measured: fde_alu_peak_probe FMA chains, double",
+                              "hbm_view": {"alg_bytes_per_launch": 16.0 * N, "gbs": gbs64, "peak": hbm,
+                                           "frac": gbs64 / hbm, "peak_source": src}}
+        # the float x2 pass of the PCG operator, the largest float kernel. Its arithmetic roof
+        # (flops at the measured float FMA rate) lies above its memory roof (8N bytes at the
+        # measured copy bandwidth), so it is reported as ALU-bound.
         ach32 = flops / (t_x2_32 * 1e-3) / 1e12
         gbs32 = 8.0 * N / (t_x2_32 * 1e-3) / 1e9
-        extras["roofline"] = {"bound": "alu", "achieved": ach32, "peak": fp32_peak, "unit": "TFLOP/s",
-                              "frac": ach32 / fp32_peak, "traffic": traffic_for("k_rows_reg_float_1024"),
-                              "kernel": "float x2 Toeplitz pass (k_rows_reg<float,1024>, autotuned tile; one launch)",
-                              "flops_per_launch": flops, "ms": t_x2_32,
-                              "peak_source": "measured: fde_alu_peak_probe FMA chains, float",
-                              "hbm_view": {"alg_bytes_per_launch": 8.0 * N, "gbs": gbs32, "peak": hbm,
-                                           "frac": gbs32 / hbm, "peak_source": src}}
-        # the double x2 pass of the verifying refinement evaluations
-        achieved = flops / (t_x2_64 * 1e-3) / 1e12
-        extras["roofline_fp64"] = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                                   "frac": achieved / fp64_peak, "traffic": traffic_for("k_rows_reg_double_1024"),
-                                   "kernel": "k_rows_reg<double,1024>: x2 Toeplitz pass in double (one launch)",
-                                   "flops_per_launch": flops, "ms": t_x2_64,
-                                   "peak_source": "measured: fde_alu_peak_probe FMA chains, double"}
+        extras["roofline_f32"] = {"bound": "alu", "achieved": ach32, "peak": fp32_peak, "unit": "TFLOP/s",
+                                  "frac": ach32 / fp32_peak, "traffic": traffic_for("k_rows_reg_float_1024"),
+                                  "kernel": "float x2 Toeplitz pass (k_rows_reg<float,1024>, autotuned tile; one "
+                                            "launch)",
+                                  "flops_per_launch": flops, "ms": t_x2_32,
+                                  "peak_source": "measured: fde_alu_peak_probe FMA chains, float",
+                                  "hbm_view": {"alg_bytes_per_launch": 8.0 * N, "gbs": gbs32, "peak": hbm,
+                                               "frac": gbs32 / hbm, "peak_source": src}}
         alg = 8.0 * N  # read x, write y (float)
         extras["matvec"] = {"kernel": "Toeplitz-FFT matvec y = B x, float (x1 pass + x2 pass)", "ms": t_b32,
                             "alg_bytes": alg, "gbs": alg / (t_b32 * 1e-3) / 1e9, "hbm_peak": hbm,
@@ -558,30 +565,41 @@ def run_kernels(args):
         b.record()
         torch.cuda.synchronize()
         out[name] = a.elapsed_time(b) / max(1, args.steps)
-    tiles = {"float": prob.tiles(), "dfloat": prob.tiles(dfloat=True)}
-    # every float tile of the two passes (threads per CTA)
+    tiles = {"float": prob.tiles(), "dfloat": prob.tiles(dfloat=True), "fp64": prob.tiles(fp64=True)}
+
+    def time3(fn):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(3):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 3
+
+    # every tile of the two passes (threads per CTA; negative: split halves), float,
+    # double-float and double
     sweep = {}
     long_rows = prob.shape[2] > 2048
-    for rows, axis in ((256, 512), (128, 256)):
-        if long_rows and rows == 128:
-            continue
-        prob.set_tiles(rows, axis)
-        for name, fn in (("x2", lambda: prob.apply_factor(x32, 2, out=y32)),
-                         ("x1", lambda: prob.apply_factor(x32, 1, out=y32))):
-            if name == "x1" and axis == 0:
+    for kind, x, y, kw, rows_list, axis_list in (
+            ("f32", x32, y32, {}, (256, 128), (512, 256)),
+            ("df", x64, y64, {"dfloat": True}, (256, -512, -256), (256, -512)),
+            ("f64", x64, y64, {"fp64": True}, (256, -512, -256), (256, -512))):
+        fk = {"dfloat": True} if kind == "df" else {}
+        for rows in rows_list:
+            if long_rows and rows in (128, -256):
                 continue
-            fn()
-            torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            for _ in range(3):
-                fn()
-            b.record()
-            torch.cuda.synchronize()
-            sweep[f"{name}_f32_tile_{rows if name == 'x2' else axis}"] = a.elapsed_time(b) / 3
+            prob.set_tiles(rows, 0, **kw)
+            sweep[f"x2_{kind}_tile_{rows}"] = time3(lambda: prob.apply_factor(x, 2, out=y, **fk))
+        for axis in axis_list:
+            prob.set_tiles(0, axis, **kw)
+            sweep[f"x1_{kind}_tile_{axis}"] = time3(lambda: prob.apply_factor(x, 1, out=y, **fk))
     prob.set_tiles(*tiles["float"])
-    print(json.dumps({"kernels_ms": out, "float_tile_sweep_ms": sweep, "workload": describe(inst, 0, 0)["workload"],
+    prob.set_tiles(*tiles["dfloat"], dfloat=True)
+    prob.set_tiles(*tiles["fp64"], fp64=True)
+    print(json.dumps({"kernels_ms": out, "tile_sweep_ms": sweep, "workload": describe(inst, 0, 0)["workload"],
                       "N": prob.N, "tiles": tiles}), flush=True)
     prob.close()
 

@@ -184,20 +184,21 @@ int fde_matvec(fde_problem* prob, int op, const fde_admm_opts* opts, int precisi
  * (double*, double-float transforms); x and y must not overlap. Errors: FDE_EINVAL. */
 int fde_apply_factor(fde_problem* prob, int axis, int op, int precision, const void* x, void* y, void* stream);
 
-/* FFT tile autotuning: times the float transform passes of this problem with
- * each tile configuration (threads per CTA, hence lines per CTA, and the
- * split-halves variant) on the problem's own sizes and keeps the fastest for all
- * later float products of `prob`. Without it a fixed default is used.
+/* FFT tile autotuning: times the float, double-float and double transform
+ * passes of this problem with each tile configuration (threads per CTA, hence
+ * lines per CTA, and the split-halves variant) on the problem's own sizes and
+ * keeps the fastest for all later products of `prob` in that arithmetic.
+ * Without it a fixed default is used.
  * fde_batch_setup calls it for every instance. Synchronises `stream`. Errors:
  * FDE_EINVAL, FDE_ECUDA. */
 int fde_autotune(fde_problem* prob, void* stream);
 
 /* Current tile choice of the x2 pass and x1 pass, for precision FDE_FP32 (the
- * float passes) or FDE_MIXED_DF (the double-float passes): threads per CTA of
- * the kernel that holds both embedding halves of a line pair in each thread
- * (float x2: 128 or 256, x1: 256 or 512; double-float: 256), or, negated, of the
- * double-float split-halves kernel whose two thread groups hold one half each
- * (x2: 256 or 512, x1: 512). */
+ * float passes), FDE_MIXED_DF (the double-float passes) or FDE_FP64 (the double
+ * passes): threads per CTA of the kernel that holds both embedding halves of a
+ * line pair in each thread (float x2: 128 or 256, x1: 256 or 512; double-float
+ * and double: 256), or, negated, of the double-float or double split-halves
+ * kernel whose two thread groups hold one half each (x2: 256 or 512, x1: 512). */
 int fde_tiles(const fde_problem* prob, int precision, int* rows_threads, int* axis_threads);
 
 /* Sets the tile choice (values as fde_tiles reports them; 0 keeps the current

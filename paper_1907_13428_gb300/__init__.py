@@ -118,6 +118,12 @@ class FdeError(RuntimeError):
         self.status = status
 
 
+def _tile_prec(dfloat: bool, fp64: bool) -> int:
+    if dfloat and fp64:
+        raise ValueError("dfloat and fp64 name different passes")
+    return FDE_MIXED_DF if dfloat else FDE_FP64 if fp64 else FDE_FP32
+
+
 def _check(status: int, what: str, allow=(FDE_OK,)):
     if status not in allow:
         raise FdeError(status, what)
@@ -221,15 +227,14 @@ class Problem:
         _check(lib().fde_autotune(self._h, _stream()), "fde_autotune")
         return self.tiles()
 
-    def set_tiles(self, rows: int = 0, axis: int = 0, dfloat: bool = False):
-        """Fix the FFT tiles of the float (or double-float) passes (fde_set_tiles;
-        negative = split-halves kernel)."""
-        _check(lib().fde_set_tiles(self._h, FDE_MIXED_DF if dfloat else FDE_FP32, rows, axis), "fde_set_tiles")
+    def set_tiles(self, rows: int = 0, axis: int = 0, dfloat: bool = False, fp64: bool = False):
+        """Fix the FFT tiles of the float (or double-float, or double) passes
+        (fde_set_tiles; negative = split-halves kernel)."""
+        _check(lib().fde_set_tiles(self._h, _tile_prec(dfloat, fp64), rows, axis), "fde_set_tiles")
 
-    def tiles(self, dfloat: bool = False):
+    def tiles(self, dfloat: bool = False, fp64: bool = False):
         a, c = ctypes.c_int(), ctypes.c_int()
-        _check(lib().fde_tiles(self._h, FDE_MIXED_DF if dfloat else FDE_FP32, ctypes.byref(a), ctypes.byref(c)),
-               "fde_tiles")
+        _check(lib().fde_tiles(self._h, _tile_prec(dfloat, fp64), ctypes.byref(a), ctypes.byref(c)), "fde_tiles")
         return a.value, c.value
 
     def apply_factor(self, x: torch.Tensor, axis: int, op: int = FDE_OP_B, out=None,

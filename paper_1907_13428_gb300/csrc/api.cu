@@ -737,8 +737,14 @@ int fde_autotune(fde_problem* P, void* stream) {
   return FDE_OK;
 }
 
+// Tile fields of one precision: float, double-float or double passes.
+static void tile_fields(fde_problem* P, int precision, int** rows, int** axis) {
+  *rows = precision == FDE_FP32 ? &P->rows_nt32 : precision == FDE_FP64 ? &P->rows_nt64 : &P->rows_ntdd;
+  *axis = precision == FDE_FP32 ? &P->axis_nt32 : precision == FDE_FP64 ? &P->axis_nt64 : &P->axis_ntdd;
+}
+
 int fde_set_tiles(fde_problem* P, int precision, int rows_threads, int axis_threads) {
-  if (!P || (precision != FDE_FP32 && precision != FDE_MIXED_DF)) return FDE_EINVAL;
+  if (!P || (precision != FDE_FP32 && precision != FDE_MIXED_DF && precision != FDE_FP64)) return FDE_EINVAL;
   const bool long_rows = P->ax[2].L > 2048;
   bool rows_ok, axis_ok;
   if (precision == FDE_FP32) {
@@ -749,17 +755,21 @@ int fde_set_tiles(fde_problem* P, int precision, int rows_threads, int axis_thre
     axis_ok = axis_threads == 0 || axis_threads == 256 || axis_threads == -512;
   }
   if (!rows_ok || !axis_ok) return FDE_EINVAL;
-  int* rf = precision == FDE_FP32 ? &P->rows_nt32 : &P->rows_ntdd;
-  int* af = precision == FDE_FP32 ? &P->axis_nt32 : &P->axis_ntdd;
+  int *rf, *af;
+  tile_fields(P, precision, &rf, &af);
   if (rows_threads) *rf = rows_threads;
   if (axis_threads) *af = axis_threads;
   return FDE_OK;
 }
 
 int fde_tiles(const fde_problem* P, int precision, int* rows_threads, int* axis_threads) {
-  if (!P || !rows_threads || !axis_threads || (precision != FDE_FP32 && precision != FDE_MIXED_DF)) return FDE_EINVAL;
-  *rows_threads = precision == FDE_FP32 ? P->rows_nt32 : P->rows_ntdd;
-  *axis_threads = precision == FDE_FP32 ? P->axis_nt32 : P->axis_ntdd;
+  if (!P || !rows_threads || !axis_threads ||
+      (precision != FDE_FP32 && precision != FDE_MIXED_DF && precision != FDE_FP64))
+    return FDE_EINVAL;
+  int *rf, *af;
+  tile_fields(const_cast<fde_problem*>(P), precision, &rf, &af);
+  *rows_threads = *rf;
+  *axis_threads = *af;
   return FDE_OK;
 }
 

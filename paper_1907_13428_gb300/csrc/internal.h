@@ -81,6 +81,9 @@ struct fde_problem {
   // tile choice of the double-float passes: 256 (both halves per thread) or split (-256/-512 x2, -512 x1)
   int rows_ntdd = 256;
   int axis_ntdd = 256;
+  // tile choice of the double passes: the same values as the double-float ones
+  int rows_nt64 = 256;
+  int axis_nt64 = 256;
   bool state_valid = false;  // the ADMM iterates hold the end of a previous solve (warm start)
 };
 

@@ -19,97 +19,10 @@
 // ny). For alpha_t = 1 the time term (psi/h_t)(x_t - x_{t-1}) (reversed for
 // B^T) is folded into the x1 pass; for alpha_t < 1 a third pass applies the
 // lower-triangular Toeplitz C_t along t (stride nx*ny) by the same embedding.
-#include <type_traits>
 
-#include "internal.h"
+#include "toeplitz.cuh"
 
 namespace fde {
-
-constexpr int kEPT = 16;  // complex elements staged per thread in an FFT pass
-
-// Epilogue of a pass, per output element idx on time slice t:
-//   out = dsc(t) * (acc[idx] + res + ct * (xt[idx] - xt[idx -/+ plane])) + addc(t) * addv[idx]
-// with dsc/addc taking v0 on slices 0..nt-2 and v1 on the last slice.
-template <typename R> struct AxisEpi {
-  R* out;
-  const R* acc;   // nullable
-  const R* xt;    // nullable: time-difference term source
-  int tdir;       // +1: x_t - x_{t-1} (B), -1: x_t - x_{t+1} (B^T)
-  R ct;           // psi / h_t
-  long long plane;
-  int nt;
-  int t_is_axis;  // strided passes: 1: time index = position along the axis; 0: = outer index
-  long long rows_per_slice;  // x2 pass: time index = row / rows_per_slice (= nx)
-  int plain;      // 1: out = res only (no acc, time term, diagonal or addend)
-  int nb_only;    // 1: time term is -ct xt[idx -/+ plane] only (+ct x_t is in the x1 symbol)
-  int has_dsc;
-  R dsc0, dsc1;
-  const R* addv;  // nullable
-  R addc0, addc1;
-  Gate gate;      // device-side skip of the whole launch (host-sync-free solve)
-};
-
-template <typename R>
-__device__ __forceinline__ void axis_store(const AxisEpi<R>& E, long long idx, int t, R res) {
-  if (E.plain) {
-    E.out[idx] = res;
-    return;
-  }
-  R v = res;
-  if (E.acc) v += E.acc[idx];
-  if (E.xt) {
-    R nb = 0;
-    if (E.tdir > 0) {
-      if (t > 0) nb = E.xt[idx - E.plane];
-    } else {
-      if (t < E.nt - 1) nb = E.xt[idx + E.plane];
-    }
-    v += E.nb_only ? -E.ct * nb : E.ct * (E.xt[idx] - nb);
-  }
-  const bool last = (t == E.nt - 1);
-  if (E.has_dsc) v *= last ? E.dsc1 : E.dsc0;
-  if (E.addv) v += (last ? E.addc1 : E.addc0) * E.addv[idx];
-  E.out[idx] = v;
-}
-
-
-// Two-phase form of axis_store for batching the epilogue's loads: epi_load
-// fetches the operands of one element, epi_finish combines and stores.
-template <typename R> struct EpiIn {
-  R acc, x0, xn, add;
-};
-
-template <typename R>
-__device__ __forceinline__ EpiIn<R> epi_load(const AxisEpi<R>& E, long long idx, int t) {
-  EpiIn<R> in{0, 0, 0, 0};
-  if (E.plain) return in;
-  if (E.acc) in.acc = E.acc[idx];
-  if (E.xt) {
-    if (!E.nb_only) in.x0 = E.xt[idx];
-    if (E.tdir > 0) {
-      if (t > 0) in.xn = E.xt[idx - E.plane];
-    } else {
-      if (t < E.nt - 1) in.xn = E.xt[idx + E.plane];
-    }
-  }
-  if (E.addv) in.add = E.addv[idx];
-  return in;
-}
-
-template <typename R>
-__device__ __forceinline__ void epi_finish(const AxisEpi<R>& E, const EpiIn<R>& in, long long idx, int t, R res) {
-  if (E.plain) {
-    E.out[idx] = res;
-    return;
-  }
-  R v = res + in.acc;
-  if (E.xt) v += E.nb_only ? -E.ct * in.xn : E.ct * (in.x0 - in.xn);
-  const bool last = (t == E.nt - 1);
-  if (E.has_dsc) v *= last ? E.dsc1 : E.dsc0;
-  if (E.addv) v += (last ? E.addc1 : E.addc0) * in.add;
-  E.out[idx] = v;
-}
-
 // ---------------------------------------------------------------------------
 // x2 axis: rows of n contiguous values; a CTA takes `pairs` row pairs and
 // builds 2*pairs complex lines of length L (pair p, half s -> line 2p+s).
@@ -212,17 +125,6 @@ __global__ void __launch_bounds__(1024) k_axis(const R* __restrict__ x, int n, i
   }
 }
 
-// Register-resident variants (defined below) used for power-of-two L >= 16.
-// R: transform arithmetic, S: storage of the vectors (S = R, or S = double with
-// double-float arithmetic R = dd).
-template <typename R, typename S>
-cudaError_t launch_rows_reg(fde_problem* P, const S* x, int conj_sym, const cplx<R>* sym, const AxisTables<R>& T,
-                            const AxisEpi<S>& E, cudaStream_t st);
-template <typename R, typename S>
-cudaError_t launch_axis_reg(int L, const S* x, int n, long long axis_stride, long long n_inner,
-                            long long outer_stride, long long n_outer, const cplx<R>* sym, const AxisTables<R>& T,
-                            int conj_sym, const AxisEpi<S>& E, int nt_choice, cudaStream_t st);
-cudaError_t toeplitz_reg_set_smem_attrs();
 
 template <typename R> static const AxisTables<R>& tables(const Axis& A);
 template <> const AxisTables<double>& tables<double>(const Axis& A) { return A.d; }
@@ -283,7 +185,7 @@ static cudaError_t launch_axis(fde_problem* P, int axis, const R* x, int conj_sy
   axis_geometry(P, axis, &axis_stride, &n_inner, &outer_stride, &n_outer);
   if (L >= 16)
     return launch_axis_reg<R, R>(L, x, A.n, axis_stride, n_inner, outer_stride, n_outer, sym ? sym : T.sym, T,
-                                 conj_sym, E, P->axis_nt32, st);
+                                 conj_sym, E, sizeof(R) == 4 ? P->axis_nt32 : P->axis_nt64, st);
   const long long total = n_outer * ((n_inner + 1) / 2);
   if (pairs > total) pairs = (int)total;
   const long long grid = (total + pairs - 1) / pairs;
@@ -450,571 +352,16 @@ cudaError_t toeplitz_set_smem_attrs() {
   if ((e = cudaFuncSetAttribute(k_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_axis<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_axis<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
-  return toeplitz_reg_set_smem_attrs();
+  if ((e = toeplitz_reg_attrs_f32())) return e;
+  if ((e = toeplitz_reg_attrs_f64())) return e;
+  return toeplitz_reg_attrs_dd();
 }
 }  // namespace fde
 
-// ===========================================================================
-// Register-resident variants (power-of-two L >= 16): each thread holds 16
-// values of both embedding halves of one complex line (fftreg.cuh).
-// ===========================================================================
-#include "fftreg.cuh"
-
 namespace fde {
 
-// x2 axis. NT threads = PAIRS row pairs x T threads per line; thread t of a
-// pair holds positions t + r T of the pair's two half-lines. Shared memory is
-// line-major with one pad element per 16 (conflict-free exchanges).
-// R: arithmetic of the transforms; S: storage type of the vectors (R, or double
-// for double-float arithmetic).
-// FULL: the lines fill the transform (n == L), so no position is out of range.
-template <typename R, int L, int NT, typename S = R, bool FULL = false>
-__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const S* __restrict__ x, long long nrows,
-                                                  int n, const cplx<R>* __restrict__ sym,
-                                                  const cplx<R>* __restrict__ tw2, const cplx<R>* __restrict__ twL,
-                                                  int conj_sym, AxisEpi<S> E) {
-  if (gate_closed(E.gate)) return;
-  using C = cplx<R>;
-  constexpr int T = L / 16, PAIRS = NT / T, LS = L + L / 16;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  const int pr = threadIdx.x / T, t = threadIdx.x - pr * T;
-  const long long ra = ((long long)blockIdx.x * PAIRS + pr) * 2, rb = ra + 1;
-  C* my = sm + pr * 2 * LS;
-  auto at = [my](int l, int pos) -> C& { return my[l * LS + pos + (pos >> 4)]; };
-  C v[2][16];
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int p = t + r * T;
-    R a = 0, b = 0;
-    if (FULL || p < n) {
-      if (ra < nrows) a = cvt_in<R, S>(x[ra * n + p]);
-      if (rb < nrows) b = cvt_in<R, S>(x[rb * n + p]);
-    }
-    v[0][r] = mk<C>(a, b);
-    v[1][r] = (FULL || p < n) ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
-  }
-  rf_forward<R, L, 2>(v, t, twL, at);
-#pragma unroll
-  for (int idx = 0; idx < 16; ++idx) {
-    const int k = rf_freq<L>(t, idx);
-#pragma unroll
-    for (int l = 0; l < 2; ++l) {
-      C w = ldg_(&sym[l * L + k]);
-      if (conj_sym) w.y = -w.y;
-      v[l][idx] = cmul(v[l][idx], w);
-    }
-  }
-  rf_inverse<R, L, 2>(v, t, twL, at);
-  const int ta = (int)(ra / E.rows_per_slice), tb = (int)(rb / E.rows_per_slice);
-  // epilogue in chunks of 4 positions: all operand loads of a chunk are issued
-  // before any arithmetic or store, so their latencies overlap
-#pragma unroll
-  for (int r0 = 0; r0 < 16; r0 += 4) {
-    EpiIn<S> ia[4], ib[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int p = t + (r0 + k) * T;
-      const bool ok = FULL || p < n;
-      ia[k] = (ok && ra < nrows) ? epi_load(E, ra * n + p, ta) : EpiIn<S>{0, 0, 0, 0};
-      ib[k] = (ok && rb < nrows) ? epi_load(E, rb * n + p, tb) : EpiIn<S>{0, 0, 0, 0};
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int p = t + (r0 + k) * T;
-      if (FULL || p < n) {
-        const C res = cadd(v[0][r0 + k], cmul(v[1][r0 + k], cconj(ldg_(&tw2[p]))));
-        if (ra < nrows) epi_finish(E, ia[k], ra * n + p, ta, cvt_out<S, R>(res.x));
-        if (rb < nrows) epi_finish(E, ib[k], rb * n + p, tb, cvt_out<S, R>(res.y));
-      }
-    }
-  }
-}
 
-// Strided axis. NT threads = CP column pairs x T; lanes run over column pairs
-// (coalesced global access). Shared memory is position-major with the two
-// halves' lines side by side; the line index is XOR-swizzled by the parity of
-// the low five position bits, which separates the two position groups of every
-// half-warp into different banks.
-template <typename R, int L, int NT, typename S = R, bool FULL = false>
-__global__ void __launch_bounds__(NT) k_axis_reg(const S* __restrict__ x, int n, long long axis_stride,
-                                                  long long n_inner, long long outer_stride, long long n_outer,
-                                                  const cplx<R>* __restrict__ sym, const cplx<R>* __restrict__ tw2,
-                                                  const cplx<R>* __restrict__ twL, int conj_sym, AxisEpi<S> E,
-                                                  int vec2) {
-  if (gate_closed(E.gate)) return;
-  using C = cplx<R>;
-  constexpr int T = L / 16, CP = NT / T, LW = 2 * CP;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  const int cl = threadIdx.x % CP, t = threadIdx.x / CP;
-  const long long npi = (n_inner + 1) / 2;
-  const long long total = n_outer * npi;
-  const long long q = (long long)blockIdx.x * CP + cl;
-  const bool valid = q < total;
-  const long long o = valid ? q / npi : 0;
-  const long long c = valid ? 2 * (q - o * npi) : 0;
-  const long long base = o * outer_stride + c;
-  const bool has_b = valid && (c + 1 < n_inner);
-  auto at = [sm, cl](int l, int pos) -> C& {
-    const int sw = (__popc(pos & 31) & 1) ? CP : 0;
-    return sm[pos * LW + ((l * CP + cl) ^ sw)];
-  };
-  C v[2][16];
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int p = t + r * T;
-    R a = 0, b = 0;
-    if (valid && (FULL || p < n)) {
-      const long long idx = base + p * axis_stride;
-      if (vec2 && has_b) {
-        const cplx<S> ab = *reinterpret_cast<const cplx<S>*>(x + idx);  // (c, c+1) as one aligned vector load
-        a = cvt_in<R, S>(ab.x);
-        b = cvt_in<R, S>(ab.y);
-      } else {
-        a = cvt_in<R, S>(x[idx]);
-        if (has_b) b = cvt_in<R, S>(x[idx + 1]);
-      }
-    }
-    v[0][r] = mk<C>(a, b);
-    v[1][r] = (FULL || p < n) ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
-  }
-  rf_forward<R, L, 2>(v, t, twL, at);
-#pragma unroll
-  for (int idx = 0; idx < 16; ++idx) {
-    const int k = rf_freq<L>(t, idx);
-#pragma unroll
-    for (int l = 0; l < 2; ++l) {
-      C w = ldg_(&sym[l * L + k]);
-      if (conj_sym) w.y = -w.y;
-      v[l][idx] = cmul(v[l][idx], w);
-    }
-  }
-  rf_inverse<R, L, 2>(v, t, twL, at);
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int p = t + r * T;
-    if (valid && (FULL || p < n)) {
-      const C res = cadd(v[0][r], cmul(v[1][r], cconj(ldg_(&tw2[p]))));
-      const long long idx = base + p * axis_stride;
-      if (E.plain && vec2 && has_b) {
-        *reinterpret_cast<cplx<S>*>(E.out + idx) = mk<cplx<S>>(cvt_out<S, R>(res.x), cvt_out<S, R>(res.y));
-        continue;
-      }
-      const int ts = E.t_is_axis ? p : (int)o;
-      axis_store(E, idx, ts, cvt_out<S, R>(res.x));
-      if (has_b) axis_store(E, idx + 1, ts, cvt_out<S, R>(res.y));
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Split-halves variants (used for double-float on double vectors): the two
-// embedding halves of a line pair are transformed by two thread groups, so a
-// thread holds the 16 values of one line (half the registers of data) and twice
-// as many warps fit on an SM (16 at 128 registers). For float the kernels that
-// hold both halves per thread are faster (measured), so only the double-float
-// instantiations are launched. After
-// the inverse transforms each group finishes every other position r (r % 2 ==
-// its half), taking the other half's term for those positions from shared
-// memory (the exchange buffers are free once the inverse has passed its last
-// barrier).
-// ---------------------------------------------------------------------------
-template <typename R> constexpr int split_min_blocks(int nt) { return (sizeof(R) == 4 ? 1024 : 512) / nt; }
-
-template <typename R, int L, int NT, typename S = R>
-__global__ void __launch_bounds__(NT, split_min_blocks<R>(NT)) k_rows_split(const S* __restrict__ x, long long nrows,
-                                                                           int n, const cplx<R>* __restrict__ sym,
-                                                                           const cplx<R>* __restrict__ tw2,
-                                                                           const cplx<R>* __restrict__ twL,
-                                                                           int conj_sym, AxisEpi<S> E) {
-  if (gate_closed(E.gate)) return;
-  using C = cplx<R>;
-  constexpr int T = L / 16, PAIRS = NT / (2 * T), LS = L + L / 16;
-  static_assert(PAIRS >= 1, "at least one row pair per CTA");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  const int pr = threadIdx.x / (2 * T);
-  const int h = (threadIdx.x / T) & 1;
-  const int t = threadIdx.x % T;
-  const long long ra = ((long long)blockIdx.x * PAIRS + pr) * 2, rb = ra + 1;
-  C* my = sm + (pr * 2 + h) * LS;
-  C* other = sm + (pr * 2 + (h ^ 1)) * LS;
-  auto at = [my](int, int pos) -> C& { return my[pos + (pos >> 4)]; };
-  C v[1][16];
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int p = t + r * T;
-    R a = 0, b = 0;
-    if (p < n) {
-      if (ra < nrows) a = cvt_in<R, S>(x[ra * n + p]);
-      if (rb < nrows) b = cvt_in<R, S>(x[rb * n + p]);
-    }
-    v[0][r] = mk<C>(a, b);
-    if (h) v[0][r] = p < n ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
-  }
-  rf_forward<R, L, 1>(v, t, twL, at);
-#pragma unroll
-  for (int idx = 0; idx < 16; ++idx) {
-    C w = ldg_(&sym[h * L + rf_freq<L>(t, idx)]);
-    if (conj_sym) w.y = -w.y;
-    v[0][idx] = cmul(v[0][idx], w);
-  }
-  rf_inverse<R, L, 1>(v, t, twL, at);
-  // the odd half's term is v conj(tw2[p]); hand over the positions the other group finishes
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int p = t + r * T;
-    if (h) v[0][r] = p < n ? cmul(v[0][r], cconj(ldg_(&tw2[p]))) : mk<C>(0, 0);
-    if ((r & 1) != h) my[p + (p >> 4)] = v[0][r];
-  }
-  __syncthreads();
-  const int ta = (int)(ra / E.rows_per_slice), tb = (int)(rb / E.rows_per_slice);
-#pragma unroll
-  for (int c0 = 0; c0 < 8; c0 += 4) {
-    EpiIn<S> ia[4], ib[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int p = t + (2 * (c0 + k) + h) * T;
-      const bool ok = p < n;
-      ia[k] = (ok && ra < nrows) ? epi_load(E, ra * n + p, ta) : EpiIn<S>{0, 0, 0, 0};
-      ib[k] = (ok && rb < nrows) ? epi_load(E, rb * n + p, tb) : EpiIn<S>{0, 0, 0, 0};
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int r = 2 * (c0 + k) + h;
-      const int p = t + r * T;
-      if (p < n) {
-        const C res = cadd(v[0][r], other[p + (p >> 4)]);
-        if (ra < nrows) epi_finish(E, ia[k], ra * n + p, ta, cvt_out<S, R>(res.x));
-        if (rb < nrows) epi_finish(E, ib[k], rb * n + p, tb, cvt_out<S, R>(res.y));
-      }
-    }
-  }
-}
-
-template <typename R, int L, int NT, typename S = R>
-__global__ void __launch_bounds__(NT, split_min_blocks<R>(NT)) k_axis_split(const S* __restrict__ x, int n,
-                                                                           long long axis_stride, long long n_inner,
-                                                                           long long outer_stride, long long n_outer,
-                                                                           const cplx<R>* __restrict__ sym,
-                                                                           const cplx<R>* __restrict__ tw2,
-                                                                           const cplx<R>* __restrict__ twL,
-                                                                           int conj_sym, AxisEpi<S> E, int vec2) {
-  if (gate_closed(E.gate)) return;
-  using C = cplx<R>;
-  constexpr int T = L / 16, CP = NT / (2 * T), LW = 2 * CP;
-  static_assert(CP >= 1, "at least one column pair per CTA");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  // lanes run over column pairs (coalesced), then over the two halves, then over t
-  const int cl = threadIdx.x % CP;
-  const int h = (threadIdx.x / CP) & 1;
-  const int t = threadIdx.x / (2 * CP);
-  const long long npi = (n_inner + 1) / 2;
-  const long long total = n_outer * npi;
-  const long long q = (long long)blockIdx.x * CP + cl;
-  const bool valid = q < total;
-  const long long o = valid ? q / npi : 0;
-  const long long c = valid ? 2 * (q - o * npi) : 0;
-  const long long base = o * outer_stride + c;
-  const bool has_b = valid && (c + 1 < n_inner);
-  auto slot = [cl](int l, int pos) -> int {
-    const int sw = (__popc(pos & 31) & 1) ? CP : 0;
-    return pos * LW + ((l * CP + cl) ^ sw);
-  };
-  auto at = [sm, h, slot](int, int pos) -> C& { return sm[slot(h, pos)]; };
-  C v[1][16];
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int p = t + r * T;
-    R a = 0, b = 0;
-    if (valid && p < n) {
-      const long long idx = base + p * axis_stride;
-      if (vec2 && has_b) {
-        const cplx<S> ab = *reinterpret_cast<const cplx<S>*>(x + idx);
-        a = cvt_in<R, S>(ab.x);
-        b = cvt_in<R, S>(ab.y);
-      } else {
-        a = cvt_in<R, S>(x[idx]);
-        if (has_b) b = cvt_in<R, S>(x[idx + 1]);
-      }
-    }
-    v[0][r] = mk<C>(a, b);
-    if (h) v[0][r] = p < n ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
-  }
-  rf_forward<R, L, 1>(v, t, twL, at);
-#pragma unroll
-  for (int idx = 0; idx < 16; ++idx) {
-    C w = ldg_(&sym[h * L + rf_freq<L>(t, idx)]);
-    if (conj_sym) w.y = -w.y;
-    v[0][idx] = cmul(v[0][idx], w);
-  }
-  rf_inverse<R, L, 1>(v, t, twL, at);
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int p = t + r * T;
-    if (h) v[0][r] = p < n ? cmul(v[0][r], cconj(ldg_(&tw2[p]))) : mk<C>(0, 0);
-    if ((r & 1) != h) sm[slot(h, p)] = v[0][r];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int r = 2 * k + h;
-    const int p = t + r * T;
-    if (valid && p < n) {
-      const C res = cadd(v[0][r], sm[slot(h ^ 1, p)]);
-      const long long idx = base + p * axis_stride;
-      if (E.plain && vec2 && has_b) {
-        *reinterpret_cast<cplx<S>*>(E.out + idx) = mk<cplx<S>>(cvt_out<S, R>(res.x), cvt_out<S, R>(res.y));
-        continue;
-      }
-      const int ts = E.t_is_axis ? p : (int)o;
-      axis_store(E, idx, ts, cvt_out<S, R>(res.x));
-      if (has_b) axis_store(E, idx + 1, ts, cvt_out<S, R>(res.y));
-    }
-  }
-}
-
-template <typename R> constexpr int rows_nt() { return 256; }
-template <typename R> constexpr int axis_nt() { return sizeof(R) == 4 ? 512 : 256; }
-
-template <typename R, int L, int NT, typename S>
-static cudaError_t launch_rows_reg_LN(fde_problem* P, const S* x, int conj_sym, const cplx<R>* sym,
-                                      const AxisTables<R>& T, const AxisEpi<S>& E, cudaStream_t st) {
-  constexpr int PAIRS = NT / (L / 16);
-  static_assert(PAIRS >= 1, "at least one row pair per CTA");
-  const long long nrows = (long long)P->nt * P->nx;
-  const long long npairs = (nrows + 1) / 2;
-  const long long grid = (npairs + PAIRS - 1) / PAIRS;
-  const size_t smem = (size_t)PAIRS * 2 * (L + L / 16) * sizeof(cplx<R>);
-  if constexpr (std::is_same<R, float>::value) {
-    if (P->ax[2].n == L) {
-      k_rows_reg<R, L, NT, S, true><<<(unsigned)grid, NT, smem, st>>>(x, nrows, L, sym, T.tw2, T.twL, conj_sym, E);
-      note_launches(1);
-      return cudaGetLastError();
-    }
-  }
-  k_rows_reg<R, L, NT, S><<<(unsigned)grid, NT, smem, st>>>(x, nrows, P->ax[2].n, sym, T.tw2, T.twL, conj_sym, E);
-  note_launches(1);
-  return cudaGetLastError();
-}
-
-template <typename R, int L, int NT, typename S>
-static cudaError_t launch_rows_split_LN(fde_problem* P, const S* x, int conj_sym, const cplx<R>* sym,
-                                        const AxisTables<R>& T, const AxisEpi<S>& E, cudaStream_t st) {
-  constexpr int PAIRS = NT / (2 * (L / 16));
-  const long long nrows = (long long)P->nt * P->nx;
-  const long long npairs = (nrows + 1) / 2;
-  const long long grid = (npairs + PAIRS - 1) / PAIRS;
-  const size_t smem = (size_t)PAIRS * 2 * (L + L / 16) * sizeof(cplx<R>);
-  k_rows_split<R, L, NT, S><<<(unsigned)grid, NT, smem, st>>>(x, nrows, P->ax[2].n, sym, T.tw2, T.twL, conj_sym, E);
-  note_launches(1);
-  return cudaGetLastError();
-}
-
-// float: the tile chosen by fde_autotune (128 or 256 threads, or the split-halves
-// variant with 256 or 512 threads, stored negated); double and double-float: 256
-template <typename R, int L, typename S>
-static cudaError_t launch_rows_reg_L(fde_problem* P, const S* x, int conj_sym, const cplx<R>* sym,
-                                     const AxisTables<R>& T, const AxisEpi<S>& E, cudaStream_t st) {
-  if constexpr (std::is_same<R, float>::value && std::is_same<S, float>::value) {
-    if constexpr (L <= 2048) {
-      if (P->rows_nt32 == 128) return launch_rows_reg_LN<R, L, 128, S>(P, x, conj_sym, sym, T, E, st);
-    }
-  }
-  if constexpr (std::is_same<R, dd>::value) {
-    if constexpr (2 * (L / 16) <= 256) {
-      if (P->rows_ntdd == -256) return launch_rows_split_LN<R, L, 256, S>(P, x, conj_sym, sym, T, E, st);
-    }
-    if (P->rows_ntdd == -512) return launch_rows_split_LN<R, L, 512, S>(P, x, conj_sym, sym, T, E, st);
-  }
-  return launch_rows_reg_LN<R, L, rows_nt<R>(), S>(P, x, conj_sym, sym, T, E, st);
-}
-
-template <typename R, int L, int NT, typename S>
-static cudaError_t launch_axis_reg_LN(const S* x, int n, long long axis_stride, long long n_inner,
-                                      long long outer_stride, long long n_outer, const cplx<R>* sym,
-                                      const AxisTables<R>& T, int conj_sym, const AxisEpi<S>& E, cudaStream_t st) {
-  constexpr int CP = NT / (L / 16);
-  static_assert(CP >= 1, "at least one column pair per CTA");
-  const long long total = n_outer * ((n_inner + 1) / 2);
-  const long long grid = (total + CP - 1) / CP;
-  const size_t smem = (size_t)L * 2 * CP * sizeof(cplx<R>);
-  const size_t al = 2 * sizeof(S);
-  const int vec2 = ((n_inner | axis_stride | outer_stride) & 1) == 0 && ((uintptr_t)x % al) == 0 &&
-                   ((uintptr_t)E.out % al) == 0;
-  if constexpr (std::is_same<R, float>::value) {
-    if (n == L) {
-      k_axis_reg<R, L, NT, S, true><<<(unsigned)grid, NT, smem, st>>>(x, L, axis_stride, n_inner, outer_stride,
-                                                                      n_outer, sym, T.tw2, T.twL, conj_sym, E, vec2);
-      note_launches(1);
-      return cudaGetLastError();
-    }
-  }
-  k_axis_reg<R, L, NT, S><<<(unsigned)grid, NT, smem, st>>>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym,
-                                                            T.tw2, T.twL, conj_sym, E, vec2);
-  note_launches(1);
-  return cudaGetLastError();
-}
-
-template <typename R, int L, int NT, typename S>
-static cudaError_t launch_axis_split_LN(const S* x, int n, long long axis_stride, long long n_inner,
-                                        long long outer_stride, long long n_outer, const cplx<R>* sym,
-                                        const AxisTables<R>& T, int conj_sym, const AxisEpi<S>& E,
-                                        cudaStream_t st) {
-  constexpr int CP = NT / (2 * (L / 16));
-  const long long total = n_outer * ((n_inner + 1) / 2);
-  const long long grid = (total + CP - 1) / CP;
-  const size_t smem = (size_t)L * 2 * CP * sizeof(cplx<R>);
-  const size_t al = 2 * sizeof(S);
-  const int vec2 = ((n_inner | axis_stride | outer_stride) & 1) == 0 && ((uintptr_t)x % al) == 0 &&
-                   ((uintptr_t)E.out % al) == 0;
-  k_axis_split<R, L, NT, S><<<(unsigned)grid, NT, smem, st>>>(x, n, axis_stride, n_inner, outer_stride, n_outer,
-                                                              sym, T.tw2, T.twL, conj_sym, E, vec2);
-  note_launches(1);
-  return cudaGetLastError();
-}
-
-template <typename R, int L, typename S>
-static cudaError_t launch_axis_reg_L(const S* x, int n, long long axis_stride, long long n_inner,
-                                     long long outer_stride, long long n_outer, const cplx<R>* sym,
-                                     const AxisTables<R>& T, int conj_sym, const AxisEpi<S>& E, int nt_choice,
-                                     cudaStream_t st) {
-  if constexpr (std::is_same<R, dd>::value) {
-    if (nt_choice == -512)
-      return launch_axis_split_LN<R, L, 512, S>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym,
-                                                E, st);
-  }
-  if constexpr (sizeof(R) == 4) {
-    if (nt_choice == 256)
-      return launch_axis_reg_LN<R, L, 256, S>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym,
-                                              E, st);
-  }
-  return launch_axis_reg_LN<R, L, axis_nt<R>(), S>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T,
-                                                   conj_sym, E, st);
-}
-
-#define FDE_FOR_EACH_L(M) M(16) M(32) M(64) M(128) M(256) M(512) M(1024) M(2048) M(4096)
-
-template <typename R, typename S>
-cudaError_t launch_rows_reg(fde_problem* P, const S* x, int conj_sym, const cplx<R>* sym, const AxisTables<R>& T,
-                            const AxisEpi<S>& E, cudaStream_t st) {
-  switch (P->ax[2].L) {
-#define FDE_CASE(LL) \
-  case LL: return launch_rows_reg_L<R, LL, S>(P, x, conj_sym, sym, T, E, st);
-    FDE_FOR_EACH_L(FDE_CASE)
-#undef FDE_CASE
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <typename R, typename S>
-cudaError_t launch_axis_reg(int L, const S* x, int n, long long axis_stride, long long n_inner,
-                            long long outer_stride, long long n_outer, const cplx<R>* sym, const AxisTables<R>& T,
-                            int conj_sym, const AxisEpi<S>& E, int nt_choice, cudaStream_t st) {
-  switch (L) {
-#define FDE_CASE(LL)                                                                                          \
-  case LL:                                                                                                    \
-    return launch_axis_reg_L<R, LL, S>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym, E, \
-                                       nt_choice, st);
-    FDE_FOR_EACH_L(FDE_CASE)
-#undef FDE_CASE
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template cudaError_t launch_rows_reg<double, double>(fde_problem*, const double*, int, const double2*,
-                                                     const AxisTables<double>&, const AxisEpi<double>&, cudaStream_t);
-template cudaError_t launch_rows_reg<float, float>(fde_problem*, const float*, int, const float2*,
-                                                   const AxisTables<float>&, const AxisEpi<float>&, cudaStream_t);
-template cudaError_t launch_rows_reg<dd, double>(fde_problem*, const double*, int, const dd2*, const AxisTables<dd>&,
-                                                 const AxisEpi<double>&, cudaStream_t);
-template cudaError_t launch_axis_reg<double, double>(int, const double*, int, long long, long long, long long,
-                                                     long long, const double2*, const AxisTables<double>&, int,
-                                                     const AxisEpi<double>&, int, cudaStream_t);
-template cudaError_t launch_axis_reg<float, float>(int, const float*, int, long long, long long, long long, long long,
-                                                   const float2*, const AxisTables<float>&, int,
-                                                   const AxisEpi<float>&, int, cudaStream_t);
-template cudaError_t launch_axis_reg<dd, double>(int, const double*, int, long long, long long, long long, long long,
-                                                 const dd2*, const AxisTables<dd>&, int, const AxisEpi<double>&, int,
-                                                 cudaStream_t);
-
-template <typename R, typename S = R>
-static cudaError_t set_attrs_reg() {
-  const int big = 200 * 1024;
-  cudaError_t e = cudaSuccess;
-#define FDE_ATTR(LL)                                                                                           \
-  if (e == cudaSuccess)                                                                                        \
-    e = cudaFuncSetAttribute(k_rows_reg<R, LL, rows_nt<R>(), S>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                             big);                                                                             \
-  if (e == cudaSuccess)                                                                                        \
-    e = cudaFuncSetAttribute(k_axis_reg<R, LL, axis_nt<R>(), S>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  FDE_FOR_EACH_L(FDE_ATTR)
-#undef FDE_ATTR
-  return e;
-}
-
-cudaError_t toeplitz_reg_set_smem_attrs() {
-  cudaError_t e = set_attrs_reg<float>();
-  if (e != cudaSuccess) return e;
-  if ((e = set_attrs_reg<double>()) != cudaSuccess) return e;
-  if ((e = set_attrs_reg<dd, double>()) != cudaSuccess) return e;
-  {
-    const int big = 200 * 1024;
-#define FDE_ATTR6(LL)                                                                                             \
-    if (e == cudaSuccess)                                                                                         \
-      e = cudaFuncSetAttribute(k_rows_split<dd, LL, 512, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                               big);                                                                              \
-    if (e == cudaSuccess)                                                                                         \
-      e = cudaFuncSetAttribute(k_axis_split<dd, LL, 512, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                               big);
-    FDE_FOR_EACH_L(FDE_ATTR6)
-#undef FDE_ATTR6
-#define FDE_ATTR7(LL)                                                                                             \
-    if (e == cudaSuccess)                                                                                         \
-      e = cudaFuncSetAttribute(k_rows_split<dd, LL, 256, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                               big);
-    FDE_ATTR7(16) FDE_ATTR7(32) FDE_ATTR7(64) FDE_ATTR7(128) FDE_ATTR7(256) FDE_ATTR7(512) FDE_ATTR7(1024)
-    FDE_ATTR7(2048)
-#undef FDE_ATTR7
-    if (e != cudaSuccess) return e;
-  }
-  const int big = 200 * 1024;
-#define FDE_ATTR2(LL)                                                                                        \
-  if (e == cudaSuccess)                                                                                      \
-    e = cudaFuncSetAttribute(k_axis_reg<float, LL, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  FDE_FOR_EACH_L(FDE_ATTR2)
-#undef FDE_ATTR2
-#define FDE_ATTR9(LL)                                                                                        \
-  if (e == cudaSuccess)                                                                                      \
-    e = cudaFuncSetAttribute(k_rows_reg<float, LL, 256, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             big);                                                                           \
-  if (e == cudaSuccess)                                                                                      \
-    e = cudaFuncSetAttribute(k_axis_reg<float, LL, 512, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             big);                                                                           \
-  if (e == cudaSuccess)                                                                                      \
-    e = cudaFuncSetAttribute(k_axis_reg<float, LL, 256, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             big);
-  FDE_FOR_EACH_L(FDE_ATTR9)
-#undef FDE_ATTR9
-#define FDE_ATTR10(LL)                                                                                       \
-  if (e == cudaSuccess)                                                                                      \
-    e = cudaFuncSetAttribute(k_rows_reg<float, LL, 128, float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             big);
-  FDE_ATTR10(16) FDE_ATTR10(32) FDE_ATTR10(64) FDE_ATTR10(128) FDE_ATTR10(256) FDE_ATTR10(512) FDE_ATTR10(1024)
-  FDE_ATTR10(2048)
-#undef FDE_ATTR10
-#define FDE_ATTR3(LL)                                                                                        \
-  if (e == cudaSuccess)                                                                                      \
-    e = cudaFuncSetAttribute(k_rows_reg<float, LL, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  FDE_ATTR3(16) FDE_ATTR3(32) FDE_ATTR3(64) FDE_ATTR3(128) FDE_ATTR3(256) FDE_ATTR3(512) FDE_ATTR3(1024)
-  FDE_ATTR3(2048)
-#undef FDE_ATTR3
-  return e;
-}
-
-// Tile autotuning of the float and double-float passes: each variant runs three
+// Tile autotuning of the float, double-float and double passes: each variant runs three
 // times on the problem's own sizes (after one warm-up launch) and the fastest is
 // kept. x, y / xd, yd: scratch vectors of length N.
 cudaError_t autotune_tiles(fde_problem* P, const float* x, float* y, const double* xd, double* yd, cudaStream_t st) {
@@ -1025,22 +372,24 @@ cudaError_t autotune_tiles(fde_problem* P, const float* x, float* y, const doubl
     cudaEventDestroy(a);
     return e;
   }
-  auto run = [&](int axis, bool dfl) -> cudaError_t {
-    return dfl ? apply_axis_raw_df(P, axis, xd, yd, 0, st)
-               : apply_axis_raw<float>(P, axis, x, y, P->ax[axis].f.sym, 0, st);
+  // arithmetic of the timed pass: 0 float, 1 double-float, 2 double
+  auto run = [&](int axis, int kind) -> cudaError_t {
+    if (kind == 1) return apply_axis_raw_df(P, axis, xd, yd, 0, st);
+    if (kind == 2) return apply_axis_raw<double>(P, axis, xd, yd, P->ax[axis].d.sym, 0, st);
+    return apply_axis_raw<float>(P, axis, x, y, P->ax[axis].f.sym, 0, st);
   };
-  auto time_it = [&](int axis, bool dfl, float* ms) -> cudaError_t {
-    cudaError_t r = run(axis, dfl);
+  auto time_it = [&](int axis, int kind, float* ms) -> cudaError_t {
+    cudaError_t r = run(axis, kind);
     if (r != cudaSuccess) return r;
     cudaEventRecord(a, st);
-    for (int k = 0; k < 3 && r == cudaSuccess; ++k) r = run(axis, dfl);
+    for (int k = 0; k < 3 && r == cudaSuccess; ++k) r = run(axis, kind);
     cudaEventRecord(b, st);
     if (r == cudaSuccess) r = cudaEventSynchronize(b);
     if (r == cudaSuccess) r = cudaEventElapsedTime(ms, a, b);
     return r;
   };
   // candidates of one tile field; negative: the split-halves variant with that many threads
-  auto tune = [&](int* field, const int* cand, int nc, int axis, bool dfl, bool short_only_mask) -> cudaError_t {
+  auto tune = [&](int* field, const int* cand, int nc, int axis, int kind, bool short_only_mask) -> cudaError_t {
     float best = 0.f, ms = 0.f;
     int pick = cand[0];
     bool first = true;
@@ -1049,7 +398,7 @@ cudaError_t autotune_tiles(fde_problem* P, const float* x, float* y, const doubl
       // the 128-thread and 256-thread split x2 tiles need a line of at most 2048
       if (short_only_mask && (c == 128 || c == -256) && P->ax[axis].L > 2048) continue;
       *field = c;
-      const cudaError_t r = time_it(axis, dfl, &ms);
+      const cudaError_t r = time_it(axis, kind, &ms);
       if (r != cudaSuccess) return r;
       if (first || ms < best) {
         best = ms;
@@ -1062,12 +411,14 @@ cudaError_t autotune_tiles(fde_problem* P, const float* x, float* y, const doubl
   };
   const int rows32[2] = {256, 128};
   const int axis32[2] = {512, 256};
-  const int rowsdd[3] = {256, -512, -256};
-  const int axisdd[2] = {256, -512};
-  if (e == cudaSuccess) e = tune(&P->rows_nt32, rows32, 2, 2, false, true);
-  if (e == cudaSuccess) e = tune(&P->axis_nt32, axis32, 2, 1, false, false);
-  if (e == cudaSuccess) e = tune(&P->rows_ntdd, rowsdd, 3, 2, true, true);
-  if (e == cudaSuccess) e = tune(&P->axis_ntdd, axisdd, 2, 1, true, false);
+  const int rows64[3] = {256, -512, -256};
+  const int axis64[2] = {256, -512};
+  if (e == cudaSuccess) e = tune(&P->rows_nt32, rows32, 2, 2, 0, true);
+  if (e == cudaSuccess) e = tune(&P->axis_nt32, axis32, 2, 1, 0, false);
+  if (e == cudaSuccess) e = tune(&P->rows_ntdd, rows64, 3, 2, 1, true);
+  if (e == cudaSuccess) e = tune(&P->axis_ntdd, axis64, 2, 1, 1, false);
+  if (e == cudaSuccess) e = tune(&P->rows_nt64, rows64, 3, 2, 2, true);
+  if (e == cudaSuccess) e = tune(&P->axis_nt64, axis64, 2, 1, 2, false);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   return e;

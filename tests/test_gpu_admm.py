@@ -56,6 +56,29 @@ def test_admm_fixed_iterations_fp64(dims, boxes):
     assert np.allclose(res, ref.residuals, rtol=1e-6, atol=1e-12)
 
 
+@pytest.mark.parametrize("prec_name", ["FDE_FP64", "FDE_MIXED_DFV"])
+def test_admm_with_split_double_tiles(prec_name):
+    """The double (and double-float) split-halves tiles inside the solve: K ADMM
+    iterations on lines that fill the transform (32 x 64) against the oracle."""
+    need_gpu()
+    F = lib()
+    inst = _instance(32, 64, 4, ua=-0.05, ub=0.05, yb=0.3)
+    K = 6
+    ref = O.admm_direct(inst, O.AdmmOptions(delta=0.8, rho=1.618), iters=K)
+    fo = F.AdmmOptions(delta=0.8, rho=1.618, max_admm=K, fixed_iters=True, inner_tol_mode=1,
+                       inner_tol=1e-13 if prec_name == "FDE_FP64" else 1e-12, precision=getattr(F, prec_name),
+                       inner_tol_mixed=1e-4)
+    prob = F.Problem(inst.params)
+    prob.set_tiles(-512, -512, fp64=True)
+    prob.set_tiles(-512, -512, dfloat=True)
+    r = prob.admm_solve(fo, dev(inst.ybar), g=dev(inst.g), ya=inst.ya, yb=inst.yb, ua=inst.ua, ub=inst.ub,
+                        allow_noconv=True)
+    prob.close()
+    tol = 1e-10 if prec_name == "FDE_FP64" else 1e-8
+    for k in ("y", "u", "p"):
+        assert relerr(host(r[k]), getattr(ref, k)) < tol, k
+
+
 @pytest.mark.parametrize("boxes", BOXES[:3])
 def test_admm_fixed_iterations_mixed(boxes):
     need_gpu()

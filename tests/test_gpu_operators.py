@@ -180,6 +180,8 @@ def test_autotuned_tiles_keep_parity(dims):
     assert rows in (128, 256) and axis in (256, 512)
     rd, ad = prob.tiles(dfloat=True)
     assert rd in (256, -256, -512) and ad in (256, -512)
+    r64, a64 = prob.tiles(fp64=True)
+    assert r64 in (256, -256, -512) and a64 in (256, -512)
     assert relerr(host(prob.matvec(dev(fi.random_field(3, (nt, nx, ny))), dfloat=True)),
                   O.apply_B(p, fi.random_field(3, (nt, nx, ny)))) < 1e-11
     x = fi.random_field(31, (nt, nx, ny))
@@ -225,6 +227,41 @@ def test_set_tiles_rejects_unknown_values():
         with pytest.raises(F.FdeError) as e:
             prob.set_tiles(*bad)
         assert e.value.status == F.FDE_EINVAL
+    for bad in ((128, 0), (0, 512), (-128, 0), (0, -256)):
+        for kw in (dict(dfloat=True), dict(fp64=True)):
+            with pytest.raises(F.FdeError) as e:
+                prob.set_tiles(*bad, **kw)
+            assert e.value.status == F.FDE_EINVAL
+    prob.close()
+
+
+@pytest.mark.parametrize("tiles", [(256, 256), (-512, -512), (-256, -512), (256, -512)])
+@pytest.mark.parametrize("dims", [(7, 5, 3), (17, 33, 6), (64, 64, 4), (100, 50, 3), (31, 200, 2), (2, 1100, 2)])
+def test_every_fp64_tile_matches_oracle(dims, tiles):
+    """Each double tile of the x2 and x1 passes (both halves per thread, split
+    halves): B, B^T and S with the epilogue, and the single factors, against the
+    oracle; lines that fill the transform (64) and ragged ones."""
+    need_gpu()
+    F = lib()
+    nx, ny, nt = dims
+    p = params(nx, ny, nt)
+    prob = F.Problem(p)
+    rows, axis = tiles
+    if ny > 2048 and rows == -256:
+        rows = 0
+    prob.set_tiles(rows, axis, fp64=True)
+    assert prob.tiles(fp64=True) == (rows or 256, axis)
+    x = fi.random_field(41, (nt, nx, ny))
+    for op, tr in ((F.FDE_OP_B, False), (F.FDE_OP_BT, True)):
+        assert relerr(host(prob.matvec(dev(x), op)), O.apply_B(p, x, transpose=tr)) < 1e-12
+    fo = F.AdmmOptions(delta=0.7, rho=1.4)
+    got = host(prob.matvec(dev(x), F.FDE_OP_S, fo))
+    assert relerr(got, O.apply_S(p, O.AdmmOptions(delta=0.7, rho=1.4), x)) < 1e-12
+    for axis_ in (1, 2):
+        X, Y = O.space_matrices(p)
+        M, along = (X, O.along_x1) if axis_ == 1 else (Y, O.along_x2)
+        ref = -O.psi_scale(p) * along(M, x)
+        assert relerr(host(prob.apply_factor(dev(x), axis_)), ref) < 1e-12
     prob.close()
 
 
@@ -248,6 +285,9 @@ def test_largest_axis_length(dims, alpha):
         for rows, axis in ((256, 256), (-512, -512)):
             prob.set_tiles(rows, axis, dfloat=True)
             assert relerr(host(prob.matvec(xd, op, dfloat=True)), ref) < 1e-11, (rows, axis)
+            prob.set_tiles(rows, axis, fp64=True)
+            assert relerr(host(prob.matvec(xd, op)), ref) < 1e-12, (rows, axis)
+        prob.set_tiles(256, 256, fp64=True)
     prob.close()
 
 
