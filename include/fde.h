@@ -49,7 +49,7 @@ enum fde_status {
   FDE_ENOCONV = -4,      /* iteration cap reached; outputs hold the last iterate           */
   FDE_EBREAKDOWN = -5,   /* PCG breakdown (p^T S p <= 0)                                   */
   FDE_ENONFINITE = -6,   /* NaN or Inf met in a reduction                                  */
-  FDE_EUNSUPPORTED = -8  /* size or mode this build does not handle                       */
+  FDE_EUNSUPPORTED = -8  /* size or mode the library does not handle                      */
 };
 
 /* Arithmetic of an operator application or of a solve. */
@@ -145,6 +145,8 @@ typedef struct fde_admm_stats {
   double max_sub_relres;     /* largest final relative residual ||b - S y||/||b|| of a sub-solve */
   int recursive_steers;      /* MIXED_DFV: corrections steered by the float PCG's recursive
                                 residual instead of an evaluated one                              */
+  double copy_in_ms;         /* fde_admm_solve_host: device time of the host-to-device copies     */
+  double copy_out_ms;        /* fde_admm_solve_host: device time of the device-to-host copies     */
 } fde_admm_stats;
 
 typedef struct fde_problem fde_problem;
@@ -237,6 +239,24 @@ int fde_admm_solve(fde_problem* prob, const fde_admm_opts* opts,
                    double ya_s, double yb_s, double ua_s, double ub_s,
                    double* y, double* u, double* p, double* zu,
                    fde_admm_stats* stats, void* stream);
+
+/* fde_admm_solve on HOST buffers: the same solve, with every array argument
+ * (ybar, g, ya, yb, ua, ub in; y, u, p, zu out; same NULL rules and lengths) in
+ * host memory. The inputs are copied to device buffers that `prob` keeps for
+ * later calls (allocated on first use, N doubles per input given), the solve
+ * runs, and the outputs are copied back before it returns. Pinned host memory
+ * (cudaHostAlloc, cudaHostRegister) is read and written by a copy kernel through
+ * its mapped device address; pageable memory goes through cudaMemcpyAsync.
+ * stats->copy_in_ms / copy_out_ms report the device time of the two copy
+ * phases. The host arrays must not be touched until the call returns. Errors:
+ * those of fde_admm_solve; the outputs are written for FDE_OK and FDE_ENOCONV
+ * only. Synchronises `stream`. */
+int fde_admm_solve_host(fde_problem* prob, const fde_admm_opts* opts,
+                        const double* ybar, const double* g,
+                        const double* ya, const double* yb, const double* ua, const double* ub,
+                        double ya_s, double yb_s, double ua_s, double ub_s,
+                        double* y, double* u, double* p, double* zu,
+                        fde_admm_stats* stats, void* stream);
 
 /* Gradient of the optimal value J* at a converged solution (envelope theorem
  * on the Lagrangian of Eq. (Generic ADMM aug Lagrangian)):

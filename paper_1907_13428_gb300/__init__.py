@@ -44,7 +44,8 @@ class fde_admm_stats(ctypes.Structure):
     _fields_ = [("admm_iters", ctypes.c_int), ("pcg_iters", ctypes.c_int), ("refine_steps", ctypes.c_int),
                 ("fp64_matvecs", ctypes.c_int), ("res_eq", ctypes.c_double), ("res_y", ctypes.c_double),
                 ("res_u", ctypes.c_double), ("objective", ctypes.c_double), ("max_sub_relres", ctypes.c_double),
-                ("recursive_steers", ctypes.c_int)]
+                ("recursive_steers", ctypes.c_int), ("copy_in_ms", ctypes.c_double),
+                ("copy_out_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -61,6 +62,8 @@ _SIGS = {
     "fde_precond": (ctypes.c_int, [_P, ctypes.POINTER(fde_admm_opts), ctypes.c_int, _P, _P, _P]),
     "fde_admm_solve": (ctypes.c_int, [_P, ctypes.POINTER(fde_admm_opts), _P, _P, _P, _P, _P, _P, _D, _D, _D, _D,
                                       _P, _P, _P, _P, ctypes.POINTER(fde_admm_stats), _P]),
+    "fde_admm_solve_host": (ctypes.c_int, [_P, ctypes.POINTER(fde_admm_opts), _P, _P, _P, _P, _P, _P, _D, _D, _D,
+                                           _D, _P, _P, _P, _P, ctypes.POINTER(fde_admm_stats), _P]),
     "fde_admm_grad": (ctypes.c_int, [_P, _P, _P, _P, _D, _P, ctypes.POINTER(ctypes.c_double), _P, _P]),
     "fde_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "fde_last_cuda_error": (ctypes.c_char_p, []),
@@ -132,6 +135,15 @@ def _check(status: int, what: str, allow=(FDE_OK,)):
 
 def _stream() -> ctypes.c_void_p:
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _host_ptr(t: Optional[torch.Tensor], n: int):
+    """Address of a contiguous float64 CPU tensor of n elements (pinned or pageable)."""
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_contiguous() or t.dtype != torch.float64 or t.numel() != n:
+        raise ValueError(f"expected a contiguous float64 CPU tensor of {n} elements")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _ptr(t: Optional[torch.Tensor], dtype=None, n=None):
@@ -288,6 +300,39 @@ class Problem:
                                  _ptr(out["y"]), _ptr(out["u"]), _ptr(out["p"]), _ptr(out["zu"]), ctypes.byref(st),
                                  _stream())
         _check(s, "fde_admm_solve", (FDE_OK, FDE_ENOCONV) if allow_noconv else (FDE_OK,))
+        res = dict(out)
+        res["stats"] = st.as_dict()
+        res["status"] = s
+        return res
+
+    def admm_solve_host(self, opts: AdmmOptions, ybar: torch.Tensor, g=None, ya=None, yb=None, ua=None, ub=None,
+                        allow_noconv: bool = False, out=None, want_p: bool = False, want_zu: bool = False):
+        """fde_admm_solve_host: ADMM on host (CPU) float64 tensors; inputs are copied in
+        and y, u (and p, z_u if asked) copied out inside the call. Bounds: None, floats or
+        CPU tensors. Pinned tensors are moved by a copy kernel. Returns dict(y, u[, p, zu],
+        stats, status) with CPU tensors (pinned when allocated here)."""
+        N = self.N
+
+        def bound(b, default):
+            if b is None or not isinstance(b, torch.Tensor):
+                return None, default if b is None else float(b)
+            return b, default
+
+        ya_t, ya_s = bound(ya, -math.inf)
+        yb_t, yb_s = bound(yb, math.inf)
+        ua_t, ua_s = bound(ua, -math.inf)
+        ub_t, ub_s = bound(ub, math.inf)
+        keys = ["y", "u"] + (["p"] if want_p else []) + (["zu"] if want_zu else [])
+        if out is None:
+            out = {k: torch.empty(N, dtype=torch.float64, pin_memory=torch.cuda.is_available()) for k in keys}
+        st = fde_admm_stats()
+        o = opts.c()
+        s = lib().fde_admm_solve_host(self._h, ctypes.byref(o), _host_ptr(ybar, N), _host_ptr(g, N),
+                                      _host_ptr(ya_t, N), _host_ptr(yb_t, N), _host_ptr(ua_t, N),
+                                      _host_ptr(ub_t, N), ya_s, yb_s, ua_s, ub_s, _host_ptr(out["y"], N),
+                                      _host_ptr(out["u"], N), _host_ptr(out.get("p"), N),
+                                      _host_ptr(out.get("zu"), N), ctypes.byref(st), _stream())
+        _check(s, "fde_admm_solve_host", (FDE_OK, FDE_ENOCONV) if allow_noconv else (FDE_OK,))
         res = dict(out)
         res["stats"] = st.as_dict()
         res["status"] = s

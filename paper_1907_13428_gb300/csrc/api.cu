@@ -800,10 +800,13 @@ int fde_precond(fde_problem* P, const fde_admm_opts* o, int precision, const voi
   return op_M<float>(P, dg, (const float*)r, (float*)z, st);
 }
 
-int fde_admm_solve(fde_problem* P, const fde_admm_opts* o, const double* ybar, const double* g, const double* ya,
-                   const double* yb, const double* ua, const double* ub, double ya_s, double yb_s, double ua_s,
-                   double ub_s, double* y, double* u, double* p, double* zu, fde_admm_stats* stats, void* stream) {
-  if (!P || !valid_opts_for(P, o) || !ybar || !y || !u) return FDE_EINVAL;
+// The ADMM solve; y, u, p, zu (device) may each be NULL (not copied out; the
+// iterates stay in V_Y, V_U, V_P, V_ZU).
+static int admm_solve_impl(fde_problem* P, const fde_admm_opts* o, const double* ybar, const double* g,
+                           const double* ya, const double* yb, const double* ua, const double* ub, double ya_s,
+                           double yb_s, double ua_s, double ub_s, double* y, double* u, double* p, double* zu,
+                           fde_admm_stats* stats, cudaStream_t st) {
+  if (!P || !valid_opts_for(P, o) || !ybar) return FDE_EINVAL;
   if (o->precision != FDE_FP64 && o->precision != FDE_MIXED && o->precision != FDE_MIXED_DF &&
       o->precision != FDE_MIXED_DFV)
     return FDE_EINVAL;
@@ -811,7 +814,6 @@ int fde_admm_solve(fde_problem* P, const fde_admm_opts* o, const double* ybar, c
   if (std::isnan(ya_s) || std::isnan(yb_s) || std::isnan(ua_s) || std::isnan(ub_s)) return FDE_EINVAL;
   for (int a = 0; a < 3; ++a)
     if (!P->ax[a].n_ok) return FDE_EUNSUPPORTED;
-  cudaStream_t st = (cudaStream_t)stream;
   const long long N = P->N;
   const Diags dg = make_diags(P, o);
 
@@ -920,13 +922,74 @@ int fde_admm_solve(fde_problem* P, const fde_admm_opts* o, const double* ybar, c
   S.res_eq = res[0];
   S.res_y = res[1];
   S.res_u = res[2];
-  CK(cudaMemcpyAsync(y, Y, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(u, U, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  if (y) CK(cudaMemcpyAsync(y, Y, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  if (u) CK(cudaMemcpyAsync(u, U, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
   if (p) CK(cudaMemcpyAsync(p, A.p, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
   if (zu) CK(cudaMemcpyAsync(zu, A.zu, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
   CK(cudaStreamSynchronize(st));
   if (stats) *stats = S;
   P->state_valid = status == FDE_OK || status == FDE_ENOCONV;
+  return status;
+}
+
+int fde_admm_solve(fde_problem* P, const fde_admm_opts* o, const double* ybar, const double* g, const double* ya,
+                   const double* yb, const double* ua, const double* ub, double ya_s, double yb_s, double ua_s,
+                   double ub_s, double* y, double* u, double* p, double* zu, fde_admm_stats* stats, void* stream) {
+  if (!y || !u) return FDE_EINVAL;
+  return admm_solve_impl(P, o, ybar, g, ya, yb, ua, ub, ya_s, yb_s, ua_s, ub_s, y, u, p, zu, stats,
+                         (cudaStream_t)stream);
+}
+
+int fde_admm_solve_host(fde_problem* P, const fde_admm_opts* o, const double* ybar, const double* g,
+                        const double* ya, const double* yb, const double* ua, const double* ub, double ya_s,
+                        double yb_s, double ua_s, double ub_s, double* y, double* u, double* p, double* zu,
+                        fde_admm_stats* stats, void* stream) {
+  if (!P || !valid_opts_for(P, o) || !ybar || !y || !u) return FDE_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long N = P->N;
+  // inputs: ybar, g, ya, yb, ua, ub -> their device copies (NULL stays NULL)
+  const double* in[6] = {ybar, g, ya, yb, ua, ub};
+  const double* dev_in[6] = {};
+  for (int k = 0; k < 6; ++k) {
+    if (!in[k]) continue;
+    if (!P->stage[k]) CK(fde_alloc(P, reinterpret_cast<void**>(&P->stage[k]), sizeof(double) * N));
+    dev_in[k] = P->stage[k];
+  }
+  cudaEvent_t ev[4] = {};
+  for (int k = 0; k < 4; ++k) {
+    const cudaError_t e = cudaEventCreate(&ev[k]);
+    if (e != cudaSuccess) {
+      for (int j = 0; j < k; ++j) cudaEventDestroy(ev[j]);
+      return cuda_status(e);
+    }
+  }
+  struct Events {
+    cudaEvent_t* e;
+    ~Events() {
+      for (int k = 0; k < 4; ++k) cudaEventDestroy(e[k]);
+    }
+  } guard{ev};
+  CK(cudaEventRecord(ev[0], st));
+  for (int k = 0; k < 6; ++k)
+    if (in[k]) CK(copy_from_host(P->stage[k], in[k], N, st));
+  CK(cudaEventRecord(ev[1], st));
+  fde_admm_stats S{};
+  const int status = admm_solve_impl(P, o, dev_in[0], dev_in[1], dev_in[2], dev_in[3], dev_in[4], dev_in[5], ya_s,
+                                     yb_s, ua_s, ub_s, nullptr, nullptr, nullptr, nullptr, &S, st);
+  if (status != FDE_OK && status != FDE_ENOCONV) return status;
+  CK(cudaEventRecord(ev[2], st));
+  CK(copy_to_host(y, P->v64[V_Y], N, st));
+  CK(copy_to_host(u, P->v64[V_U], N, st));
+  if (p) CK(copy_to_host(p, P->v64[V_P], N, st));
+  if (zu) CK(copy_to_host(zu, P->v64[V_ZU], N, st));
+  CK(cudaEventRecord(ev[3], st));
+  CK(cudaStreamSynchronize(st));
+  float ms_in = 0.f, ms_out = 0.f;
+  CK(cudaEventElapsedTime(&ms_in, ev[0], ev[1]));
+  CK(cudaEventElapsedTime(&ms_out, ev[2], ev[3]));
+  S.copy_in_ms = ms_in;
+  S.copy_out_ms = ms_out;
+  if (stats) *stats = S;
   return status;
 }
 

@@ -66,6 +66,7 @@ struct fde_problem {
   float* v32[12] = {};
   double2* spec64 = nullptr;
   float2* spec32 = nullptr;
+  double* stage[6] = {};       // device copies of the host inputs of fde_admm_solve_host, allocated on first use
   double* mr64 = nullptr;      // saddle-point (MINRES) workspace, allocated on first use
   float* mr32 = nullptr;
   double* partials = nullptr;  // reduction partial sums
@@ -140,6 +141,11 @@ cudaError_t apply_axis_raw(fde_problem* P, int axis, const R* x, R* y, const cpl
 
 // apply_axis_raw<double> with the axis' own symbol in double-float arithmetic.
 cudaError_t apply_axis_raw_df(fde_problem* P, int axis, const double* x, double* y, int conj_sym, cudaStream_t st);
+
+// n doubles between a host buffer and device memory (hostio.cu): a copy kernel
+// through the mapped address of pinned memory, cudaMemcpyAsync for pageable memory.
+cudaError_t copy_from_host(double* dev_dst, const double* host_src, long long n, cudaStream_t st);
+cudaError_t copy_to_host(double* host_dst, const double* dev_src, long long n, cudaStream_t st);
 
 // Times the float and double-float tile variants of the x2 and x1 passes on this
 // problem (x, y and xd, yd: scratch vectors of length N) and keeps the fastest in

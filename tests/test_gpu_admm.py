@@ -299,3 +299,56 @@ def test_coincident_bounds_fix_the_control():
     assert float((r["zu"] - 0.01).abs().max()) == 0.0
     for k in ("y", "u", "p"):
         assert relerr(host(r[k]), getattr(ref, k)) < 1e-10, k
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("prec_name", ["FDE_FP64", "FDE_MIXED_DFV"])
+def test_host_buffer_solve_matches_device_solve(prec_name, pinned):
+    """fde_admm_solve_host (inputs and outputs in host memory; pinned buffers moved by
+    the copy kernel, pageable ones by cudaMemcpyAsync) returns exactly what
+    fde_admm_solve returns on device copies of the same arrays, with array and
+    scalar bounds, and matches the oracle."""
+    need_gpu()
+    F = lib()
+    inst = _instance(20, 36, 5, ua=-0.05, ub=0.05)
+    yb = 0.3 + 0.05 * fi.random_field(71, (5, 20, 36))
+    K = 5
+    fo = F.AdmmOptions(delta=0.8, rho=1.618, max_admm=K, fixed_iters=True, inner_tol_mode=1, inner_tol=1e-12,
+                       precision=getattr(F, prec_name), inner_tol_mixed=1e-4)
+
+    def host(a):
+        t = torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel())
+        return t.pin_memory() if pinned else t.clone()
+
+    prob = F.Problem(inst.params)
+    d = prob.admm_solve(fo, dev(inst.ybar), g=dev(inst.g), yb=dev(yb), ua=inst.ua, ub=inst.ub, allow_noconv=True)
+    d = {k: d[k].cpu() for k in ("y", "u", "p", "zu")}
+    out = None if pinned else {k: torch.empty(inst.params.N, dtype=torch.float64) for k in ("y", "u", "p", "zu")}
+    h = prob.admm_solve_host(fo, host(inst.ybar), g=host(inst.g), yb=host(yb), ua=inst.ua, ub=inst.ub,
+                             allow_noconv=True, out=out, want_p=True, want_zu=True)
+    prob.close()
+    for k in ("y", "u", "p", "zu"):
+        assert not h[k].is_cuda and torch.equal(h[k], d[k]), k
+    assert h["stats"]["copy_in_ms"] > 0 and h["stats"]["copy_out_ms"] > 0
+    ref = O.admm_direct(fi.FdeInstance(inst.params, inst.ybar, inst.g, None, yb, inst.ua, inst.ub, inst.seed),
+                        O.AdmmOptions(delta=0.8, rho=1.618), iters=K)
+    tol = 1e-10 if prec_name == "FDE_FP64" else 1e-8
+    assert relerr(h["y"].numpy(), ref.y) < tol and relerr(h["u"].numpy(), ref.u) < tol
+
+
+def test_host_buffer_solve_rejects_bad_buffers():
+    need_gpu()
+    F = lib()
+    p = params(8, 8, 2)
+    prob = F.Problem(p)
+    fo = F.AdmmOptions(max_admm=2, precision=F.FDE_FP64)
+    with pytest.raises(F.FdeError) as e:
+        prob.admm_solve_host(fo, None)
+    assert e.value.status == F.FDE_EINVAL
+    with pytest.raises(ValueError):
+        prob.admm_solve_host(fo, torch.zeros(prob.N, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        prob.admm_solve_host(fo, torch.zeros(prob.N + 1, dtype=torch.float64))
+    r = prob.admm_solve_host(fo, torch.zeros(prob.N, dtype=torch.float64), allow_noconv=True)
+    assert float(r["y"].abs().max()) == 0.0 and float(r["u"].abs().max()) == 0.0
+    prob.close()
