@@ -187,16 +187,45 @@ __global__ void __launch_bounds__(NT, split_min_blocks<R>(NT)) k_rows_split(cons
   C* other = sm + (pr * 2 + (h ^ 1)) * LS;
   auto at = [my](int, int pos) -> C& { return my[pos + (pos >> 4)]; };
   C v[1][16];
+  if constexpr (!std::is_same<R, S>::value) {
+    // both groups need the whole line pair: each converts the positions of its own
+    // parity (r & 1 == h) and takes the others from the other group's line buffer
 #pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int p = t + r * T;
-    R a = 0, b = 0;
-    if (FULL || p < n) {
-      if (ra < nrows) a = cvt_in<R, S>(x[ra * n + p]);
-      if (rb < nrows) b = cvt_in<R, S>(x[rb * n + p]);
+    for (int r = 0; r < 16; ++r) {
+      if ((r & 1) != h) continue;
+      const int p = t + r * T;
+      R a = 0, b = 0;
+      if (FULL || p < n) {
+        if (ra < nrows) a = cvt_in<R, S>(x[ra * n + p]);
+        if (rb < nrows) b = cvt_in<R, S>(x[rb * n + p]);
+      }
+      v[0][r] = mk<C>(a, b);
+      my[p + (p >> 4)] = v[0][r];
     }
-    v[0][r] = mk<C>(a, b);
-    if (h) v[0][r] = (FULL || p < n) ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int p = t + r * T;
+      if ((r & 1) != h) v[0][r] = other[p + (p >> 4)];
+    }
+    __syncthreads();  // the transform's first exchange overwrites the line buffers
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int p = t + r * T;
+      if (h) v[0][r] = (FULL || p < n) ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int p = t + r * T;
+      R a = 0, b = 0;
+      if (FULL || p < n) {
+        if (ra < nrows) a = cvt_in<R, S>(x[ra * n + p]);
+        if (rb < nrows) b = cvt_in<R, S>(x[rb * n + p]);
+      }
+      v[0][r] = mk<C>(a, b);
+      if (h) v[0][r] = (FULL || p < n) ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
+    }
   }
   rf_forward<R, L, 1>(v, t, twL, at);
 #pragma unroll
