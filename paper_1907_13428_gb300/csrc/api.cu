@@ -969,21 +969,33 @@ int fde_admm_solve_host(fde_problem* P, const fde_admm_opts* o, const double* yb
       for (int k = 0; k < 4; ++k) cudaEventDestroy(e[k]);
     }
   } guard{ev};
-  CK(cudaEventRecord(ev[0], st));
+  // once a copy is queued, every return waits for the stream: no queued copy may still
+  // read or write the caller's host arrays after the call returns
+  auto drain = [st](int status) {
+    cudaStreamSynchronize(st);
+    return status;
+  };
+#define CKD(expr)                                          \
+  do {                                                     \
+    cudaError_t _e = (expr);                               \
+    if (_e != cudaSuccess) return drain(cuda_status(_e));  \
+  } while (0)
+  CKD(cudaEventRecord(ev[0], st));
   for (int k = 0; k < 6; ++k)
-    if (in[k]) CK(copy_from_host(P->stage[k], in[k], N, st));
-  CK(cudaEventRecord(ev[1], st));
+    if (in[k]) CKD(copy_from_host(P->stage[k], in[k], N, st));
+  CKD(cudaEventRecord(ev[1], st));
   fde_admm_stats S{};
   const int status = admm_solve_impl(P, o, dev_in[0], dev_in[1], dev_in[2], dev_in[3], dev_in[4], dev_in[5], ya_s,
                                      yb_s, ua_s, ub_s, nullptr, nullptr, nullptr, nullptr, &S, st);
-  if (status != FDE_OK && status != FDE_ENOCONV) return status;
-  CK(cudaEventRecord(ev[2], st));
-  CK(copy_to_host(y, P->v64[V_Y], N, st));
-  CK(copy_to_host(u, P->v64[V_U], N, st));
-  if (p) CK(copy_to_host(p, P->v64[V_P], N, st));
-  if (zu) CK(copy_to_host(zu, P->v64[V_ZU], N, st));
-  CK(cudaEventRecord(ev[3], st));
-  CK(cudaStreamSynchronize(st));
+  if (status != FDE_OK && status != FDE_ENOCONV) return drain(status);
+  CKD(cudaEventRecord(ev[2], st));
+  CKD(copy_to_host(y, P->v64[V_Y], N, st));
+  CKD(copy_to_host(u, P->v64[V_U], N, st));
+  if (p) CKD(copy_to_host(p, P->v64[V_P], N, st));
+  if (zu) CKD(copy_to_host(zu, P->v64[V_ZU], N, st));
+  CKD(cudaEventRecord(ev[3], st));
+  CKD(cudaStreamSynchronize(st));
+#undef CKD
   float ms_in = 0.f, ms_out = 0.f;
   CK(cudaEventElapsedTime(&ms_in, ev[0], ev[1]));
   CK(cudaEventElapsedTime(&ms_out, ev[2], ev[3]));
