@@ -70,3 +70,34 @@ def test_status_strings_without_gpu():
     assert L.fde_strerror(0) == b"ok"
     assert b"invalid" in L.fde_strerror(-1)
     assert L.fde_size(None) == 0
+
+
+def test_binding_tile_precision_and_host_buffer_checks():
+    """Host-side argument checks of the binding: the tile precision selector and the
+    host-buffer validation of admm_solve_host (no GPU call is made)."""
+    import torch
+
+    import paper_1907_13428_gb300 as F
+    assert F._tile_prec(False, False) == F.FDE_FP32
+    assert F._tile_prec(True, False) == F.FDE_MIXED_DF
+    assert F._tile_prec(False, True) == F.FDE_FP64
+    with pytest.raises(ValueError):
+        F._tile_prec(True, True)
+    t = torch.zeros(12, dtype=torch.float64)
+    assert F._host_ptr(None, 12) is None
+    assert F._host_ptr(t, 12).value == t.data_ptr()
+    for bad in (torch.zeros(11, dtype=torch.float64), torch.zeros(12, dtype=torch.float32),
+                torch.zeros(24, dtype=torch.float64)[::2]):
+        with pytest.raises(ValueError):
+            F._host_ptr(bad, 12)
+
+
+def test_host_solve_rejects_null_arguments_without_gpu():
+    """fde_admm_solve_host validates its arguments before any CUDA call."""
+    F, L = _lib()
+    st = F.fde_admm_stats()
+    o = F.AdmmOptions().c()
+    buf = (ctypes.c_double * 4)()
+    args = [None, ctypes.byref(o), buf, None, None, None, None, None, 0.0, 0.0, 0.0, 0.0, buf, buf, None, None,
+            ctypes.byref(st), None]
+    assert L.fde_admm_solve_host(*args) == F.FDE_EINVAL
