@@ -258,13 +258,35 @@ int fde_admm_solve_host(fde_problem* prob, const fde_admm_opts* opts,
                         double* y, double* u, double* p, double* zu,
                         fde_admm_stats* stats, void* stream);
 
+/* The iterates of Algorithm 1 (Section 3.1, psi-scaled as in Section 6.1) that
+ * the last fde_admm_solve / fde_admm_solve_host on `prob` ended with (also
+ * after FDE_ENOCONV), or that fde_admm_set_iterates loaded: the state y and
+ * control u, their projected copies z_y and z_u, the multiplier p of
+ * B y + psi u = psi g and the multipliers w_y, w_u of y = z_y and
+ * psi u = psi z_u. At a converged solution w_y is the state-box multiplier
+ * that the adjoint equation of fde_admm_grad needs. Each output is a DEVICE
+ * array of N doubles or NULL (not copied). Errors: FDE_EINVAL (no solve has
+ * left iterates on `prob`, or the last one failed), FDE_ECUDA. Synchronises
+ * `stream`. */
+int fde_admm_get_iterates(const fde_problem* prob, double* y, double* u, double* zy, double* zu, double* p,
+                          double* wy, double* wu, void* stream);
+
+/* Load the iterates a solve with opts->warm_start = 1 starts from (same
+ * arrays as fde_admm_get_iterates, DEVICE, N doubles each; NULL = zero), for
+ * instance the end of a solve of a neighbouring problem (continuation in the
+ * coefficients). Computes B y of the given y for the first ADMM step.
+ * Errors: FDE_EINVAL, FDE_ECUDA. Synchronises `stream`. */
+int fde_admm_set_iterates(fde_problem* prob, const double* y, const double* u, const double* zy, const double* zu,
+                          const double* p, const double* wy, const double* wu, void* stream);
+
 /* Gradient of the optimal value J* at a converged solution (envelope theorem
  * on the Lagrangian of Eq. (Generic ADMM aug Lagrangian)):
  *   d(J^*)/dybar = -J1 (y* - ybar)                      -> dJ_dybar (device, N, may be NULL)
  *   d(J^*)/d{d+, d-, e+, e-} = -psi p*^T (I (x) L (x) I) y* with L = L_x, L_x^T on x1
  *                           and L_y, L_y^T on x2       -> dJ_dcoef[4] (HOST doubles)
  * p* is obtained by solving the adjoint equation B^T p = -J1 (y* - ybar) - w_y
- * (w_y: the state-box multiplier, NULL = 0) with CG on B B^T preconditioned by
+ * (w_y: the state-box multiplier of the converged solve, fde_admm_get_iterates;
+ * NULL = 0, correct only when no state bound is active) with CG on B B^T preconditioned by
  * C_3 C_3^T, to relative residual `tol` (<= 0 selects 1e-12); p_out (device, N,
  * may be NULL) receives it. Double precision throughout. Errors: FDE_EINVAL,
  * FDE_ENOCONV, FDE_ECUDA. Synchronises `stream`. */

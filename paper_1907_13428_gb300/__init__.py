@@ -65,6 +65,8 @@ _SIGS = {
     "fde_admm_solve_host": (ctypes.c_int, [_P, ctypes.POINTER(fde_admm_opts), _P, _P, _P, _P, _P, _P, _D, _D, _D,
                                            _D, _P, _P, _P, _P, ctypes.POINTER(fde_admm_stats), _P]),
     "fde_admm_grad": (ctypes.c_int, [_P, _P, _P, _P, _D, _P, ctypes.POINTER(ctypes.c_double), _P, _P]),
+    "fde_admm_get_iterates": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "fde_admm_set_iterates": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "fde_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "fde_last_cuda_error": (ctypes.c_char_p, []),
     "fde_kernel_launches": (ctypes.c_longlong, []),
@@ -338,6 +340,30 @@ class Problem:
         res["status"] = s
         return res
 
+    ITERATES = ("y", "u", "zy", "zu", "p", "wy", "wu")
+
+    def iterates(self, names: Sequence[str] = ITERATES, device=None) -> dict:
+        """Iterates the last solve on this problem ended with (fde_admm_get_iterates):
+        a dict of CUDA float64 tensors for the requested names among y, u, zy, zu, p,
+        wy (state-box multiplier), wu."""
+        bad = set(names) - set(self.ITERATES)
+        if bad:
+            raise ValueError(f"unknown iterates {sorted(bad)}")
+        dev = torch.device("cuda") if device is None else device
+        out = {k: torch.empty(self.N, dtype=torch.float64, device=dev) for k in names}
+        _check(lib().fde_admm_get_iterates(self._h, *[_ptr(out.get(k)) for k in self.ITERATES], _stream()),
+               "fde_admm_get_iterates")
+        return out
+
+    def set_iterates(self, it: dict):
+        """Load the iterates a warm-started solve begins from (fde_admm_set_iterates);
+        missing names are zero."""
+        bad = set(it) - set(self.ITERATES)
+        if bad:
+            raise ValueError(f"unknown iterates {sorted(bad)}")
+        _check(lib().fde_admm_set_iterates(self._h, *[_ptr(it.get(k), torch.float64, self.N) for k in self.ITERATES],
+                                           _stream()), "fde_admm_set_iterates")
+
     def admm_grad(self, y: torch.Tensor, ybar: torch.Tensor, wy: Optional[torch.Tensor] = None, tol: float = 1e-12):
         """Returns (dJ/dybar [N], dJ/d(d+, d-, e+, e-) [4] float64 CPU tensor, adjoint p [N])."""
         N = self.N
@@ -405,22 +431,28 @@ class Batch:
 class FdeAdmmFn(torch.autograd.Function):
     """J*(ybar, d+, d-, e+, e-): optimal value of the ADMM problem. The backward
     pass is the library's adjoint (fde_admm_grad): gradient of J* with respect
-    to the desired state and the four diffusion coefficients."""
+    to the desired state and the four diffusion coefficients. The adjoint
+    equation B^T p = -J1 (y* - ybar) - w_y* takes the state-box multiplier w_y*
+    of the converged solve (fde_admm_get_iterates), so active state bounds are
+    accounted for. The problem handle lives as long as the autograd graph, so a
+    second backward (retain_graph) works."""
 
     @staticmethod
     def forward(ctx, ybar, coef, params, opts, bounds):
         q = dataclasses.replace(params, dp=float(coef[0]), dm=float(coef[1]), ep=float(coef[2]), em=float(coef[3]))
         prob = Problem(q)
         r = prob.admm_solve(opts, ybar.contiguous().view(-1), **bounds)
+        state_box = bounds.get("ya") is not None or bounds.get("yb") is not None
+        wy = prob.iterates(("wy",), device=ybar.device)["wy"] if state_box else None
         ctx.prob = prob
+        ctx.wy = wy
         ctx.save_for_backward(r["y"], ybar)
         return torch.tensor(r["stats"]["objective"], dtype=torch.float64, device=ybar.device)
 
     @staticmethod
     def backward(ctx, gout):
         y, ybar = ctx.saved_tensors
-        dJ, dcoef, _ = ctx.prob.admm_grad(y, ybar.contiguous().view(-1))
-        ctx.prob.close()
+        dJ, dcoef, _ = ctx.prob.admm_grad(y, ybar.contiguous().view(-1), wy=ctx.wy)
         return (gout * dJ.view_as(ybar), gout.cpu() * dcoef, None, None, None)
 
 

@@ -1005,6 +1005,43 @@ int fde_admm_solve_host(fde_problem* P, const fde_admm_opts* o, const double* yb
   return status;
 }
 
+int fde_admm_get_iterates(const fde_problem* P, double* y, double* u, double* zy, double* zu, double* p, double* wy,
+                          double* wu, void* stream) {
+  if (!P) return FDE_EINVAL;
+  if (!P->state_valid) return FDE_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * (size_t)P->N;
+  double* out[7] = {y, u, zy, zu, p, wy, wu};
+  const int slot[7] = {V_Y, V_U, V_ZY, V_ZU, V_P, V_WY, V_WU};
+  for (int k = 0; k < 7; ++k)
+    if (out[k]) CK(cudaMemcpyAsync(out[k], P->v64[slot[k]], bytes, cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return FDE_OK;
+}
+
+int fde_admm_set_iterates(fde_problem* P, const double* y, const double* u, const double* zy, const double* zu,
+                          const double* p, const double* wy, const double* wu, void* stream) {
+  if (!P) return FDE_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long N = P->N;
+  const double* in[7] = {y, u, zy, zu, p, wy, wu};
+  const int slot[7] = {V_Y, V_U, V_ZY, V_ZU, V_P, V_WY, V_WU};
+  P->state_valid = false;
+  for (int k = 0; k < 7; ++k) {
+    if (in[k]) {
+      CK(cudaMemcpyAsync(P->v64[slot[k]], in[k], sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    } else {
+      CK(fill<double>(P->v64[slot[k]], 0.0, N, st));
+    }
+  }
+  // a warm-started solve expects V_BY = B y of the starting y (double product)
+  auto s = scratch64(P);
+  CK(apply_B<double>(P, 0, P->v64[V_Y], P->v64[V_BY], nullptr, nullptr, nullptr, s.t1, s.t2, st));
+  CK(cudaStreamSynchronize(st));
+  P->state_valid = true;
+  return FDE_OK;
+}
+
 int fde_admm_grad(fde_problem* P, const double* y, const double* ybar, const double* wy, double tol, double* dJ_dybar,
                   double* dJ_dcoef, double* p_out, void* stream) {
   if (!P || !y || !ybar || !dJ_dcoef) return FDE_EINVAL;

@@ -3,7 +3,8 @@
 // so a kernel reads or writes it directly over the CPU-GPU link: the SMs move
 // the data instead of the copy engines, whose transfers measured 3-8x slower
 // right after a long solve (58-68 GB/s out, 26 GB/s in, against 192 and 210 GB/s
-// for the kernel). Pageable host memory goes through cudaMemcpyAsync.
+// for the kernel). Pageable host memory, and device memory of another GPU, go
+// through cudaMemcpyAsync.
 #include "internal.h"
 
 namespace fde {
@@ -36,9 +37,17 @@ cudaError_t device_address(const void* host, const void** dev, bool* mapped) {
     if ((e = cudaHostGetDevicePointer(&d, const_cast<void*>(host), 0)) != cudaSuccess) return e;
     *dev = d;
     *mapped = true;
-  } else if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+  } else if (at.type == cudaMemoryTypeManaged) {
     *dev = host;
     *mapped = true;
+  } else if (at.type == cudaMemoryTypeDevice) {
+    // device memory of this GPU is used in place; another GPU's memory is not
+    // addressable by this GPU's kernels without peer access, so it goes through
+    // cudaMemcpyAsync (cudaMemcpyDefault resolves the direction by address)
+    int cur = -1;
+    if ((e = cudaGetDevice(&cur)) != cudaSuccess) return e;
+    *dev = at.device == cur ? host : nullptr;
+    *mapped = at.device == cur;
   } else {
     *dev = nullptr;
     *mapped = false;
@@ -65,7 +74,7 @@ cudaError_t copy_from_host(double* dev_dst, const double* host_src, long long n,
   cudaError_t e = device_address(host_src, &src, &mapped);
   if (e != cudaSuccess) return e;
   if (mapped) return copy_kernel(dev_dst, static_cast<const double*>(src), n, st);
-  return cudaMemcpyAsync(dev_dst, host_src, sizeof(double) * n, cudaMemcpyHostToDevice, st);
+  return cudaMemcpyAsync(dev_dst, host_src, sizeof(double) * n, cudaMemcpyDefault, st);
 }
 
 cudaError_t copy_to_host(double* host_dst, const double* dev_src, long long n, cudaStream_t st) {
@@ -74,7 +83,7 @@ cudaError_t copy_to_host(double* host_dst, const double* dev_src, long long n, c
   cudaError_t e = device_address(host_dst, &dst, &mapped);
   if (e != cudaSuccess) return e;
   if (mapped) return copy_kernel(static_cast<double*>(const_cast<void*>(dst)), dev_src, n, st);
-  return cudaMemcpyAsync(host_dst, dev_src, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+  return cudaMemcpyAsync(host_dst, dev_src, sizeof(double) * n, cudaMemcpyDefault, st);
 }
 
 }  // namespace fde

@@ -101,3 +101,30 @@ def test_host_solve_rejects_null_arguments_without_gpu():
     args = [None, ctypes.byref(o), buf, None, None, None, None, None, 0.0, 0.0, 0.0, 0.0, buf, buf, None, None,
             ctypes.byref(st), None]
     assert L.fde_admm_solve_host(*args) == F.FDE_EINVAL
+
+
+def test_setup_rejects_invalid_parameters_without_gpu():
+    """fde_setup checks the problem description before any CUDA call: orders
+    outside (1, 2) and (0, 1], empty or oversized axes, a non-positive gamma or
+    final time, negative coefficients and unknown modes."""
+    F, L = _lib()
+    good = dict(nx=8, ny=8, nt=4, T=1.0, beta_x=1.5, beta_y=1.5, alpha_t=1.0, dp=1.0, dm=0.5, ep=0.8, em=0.3,
+                gamma=1e-3, weights=0, time_step_mode=0)
+    bad = [dict(beta_x=1.0), dict(beta_y=2.0), dict(alpha_t=0.0), dict(alpha_t=1.5), dict(nx=0), dict(nt=0),
+           dict(gamma=0.0), dict(T=0.0), dict(dm=-1.0), dict(weights=2), dict(time_step_mode=3),
+           dict(beta_x=float("nan"))]
+    for kw in bad:
+        ps = F.fde_params(**{**good, **kw})
+        h = ctypes.c_void_p()
+        assert L.fde_setup(ctypes.byref(ps), ctypes.byref(h), None) == F.FDE_EINVAL, kw
+        assert not h.value
+    ps = F.fde_params(**{**good, "nx": 4097})
+    h = ctypes.c_void_p()
+    assert L.fde_setup(ctypes.byref(ps), ctypes.byref(h), None) == F.FDE_EUNSUPPORTED
+    assert L.fde_setup(None, ctypes.byref(h), None) == F.FDE_EINVAL
+
+
+def test_iterate_calls_reject_null_problem_without_gpu():
+    F, L = _lib()
+    assert L.fde_admm_get_iterates(None, None, None, None, None, None, None, None, None) == F.FDE_EINVAL
+    assert L.fde_admm_set_iterates(None, None, None, None, None, None, None, None, None) == F.FDE_EINVAL
