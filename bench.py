@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "medium", "small", "slab", "batch"])
+    ap.add_argument("--workload", default="large", choices=["large", "medium", "small", "slab", "batch", "paper-table5"])
     ap.add_argument("--admm-iters", type=int, default=20)
     ap.add_argument("--sub-tol", type=float, default=1e-8)
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 comparison, e2e and CPU baseline")
@@ -692,7 +692,9 @@ def run_kernels(args):
                      ("x2_pass_f32", lambda: prob.apply_factor(x32, 2, out=y32)),
                      ("x1_pass_f32", lambda: prob.apply_factor(x32, 1, out=y32)),
                      ("x2_pass_df", lambda: prob.apply_factor(x64, 2, out=y64, dfloat=True)),
-                     ("x1_pass_df", lambda: prob.apply_factor(x64, 1, out=y64, dfloat=True))):
+                     ("x1_pass_df", lambda: prob.apply_factor(x64, 1, out=y64, dfloat=True)),
+                     ("precond_f32", lambda: prob.precond(x32, out=y32)),
+                     ("B_f32", lambda: prob.matvec(x32, F.FDE_OP_B, out=y32))):
         fn()
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
@@ -742,6 +744,69 @@ def run_kernels(args):
     prob.close()
 
 
+# Table 5 of the paper (box constraints on both variables, varying grid size; beta = 1.3,
+# alpha = 0.7, gamma = 1e-4, y_a = -4, u_a = -350): n, delta, misfit, dual infeasibility,
+# average PCG iterations, ADMM iterations, MATLAB time in seconds on a 6-core i7.
+PAPER_TABLE5 = [(8, 2.0, 0.387, 5.23e-4, 12, 86, 1.89), (16, 2.0, 0.502, 8.68e-5, 13, 58, 6.06),
+                (32, 0.4, 0.609, 2.94e-4, 16, 62, 75.04), (50, 0.4, 0.645, 1.99e-4, 18, 126, 412.66),
+                (64, 0.1, 0.658, 3.34e-3, 17, 97, 987.12), (80, 0.1, 0.665, 4.31e-3, 17, 102, 1135.83),
+                (100, 0.1, 0.670, 4.91e-3, 17, 119, 2436.17), (128, 0.1, 0.673, 3.49e-3, 17, 169, 9077.08)]
+
+
+def run_paper_table5(args):
+    """The grid sweep of Table 5 in the paper's own setting (Section 6.1: n^3 grid,
+    h_t = h_x, Riesz beta = 1.3, time order 0.7, the analytic desired state, symmetric
+    boxes y in [-4, 4], u in [-350, 350], rho = 1.618, ADMM tolerance 1e-4, the inner
+    rule 0.05 max{min residuals, 1e-4}), solved on the GPU in FP64 and in mixed
+    precision. Per row: ADMM iterations, average PCG iterations per ADMM iteration,
+    the misfit E_L2, the dual infeasibility and the solve time, beside the paper's
+    printed row (context: its numbers come from MATLAB's pcg on a 6-core CPU)."""
+    import torch
+    import fde_inputs as fi
+    import paper_1907_13428_gb300 as F
+    dev = torch.device("cuda", 0)
+    rows = []
+    for n, delta, e_p, dinf_p, pcg_p, admm_p, t_p in PAPER_TABLE5:
+        c = -1.0 / (2.0 * math.cos(1.3 * math.pi / 2.0))
+        p = fi.FdeParams(nx=n, ny=n, nt=n, T=1.0, beta_x=1.3, beta_y=1.3, alpha_t=0.7, dp=c, dm=c, ep=c, em=c,
+                         gamma=1e-4, weights=0, time_step_mode=1)
+        ybar_np = fi.desired_state_paper(p)
+        prob = F.Problem(p)
+        ybar = torch.as_tensor(ybar_np.ravel(), device=dev)
+        bounds = dict(ya=-4.0, yb=4.0, ua=-350.0, ub=350.0)
+        row = {"n": n, "N": p.N, "delta": delta,
+               "paper": {"E_L2": e_p, "dual_inf": dinf_p, "pcg_avg": pcg_p, "admm": admm_p, "time_s": t_p}}
+        for name, prec in (("fp64", F.FDE_FP64), ("mixed_dfv", F.FDE_MIXED_DFV)):
+            o = F.AdmmOptions(delta=delta, rho=1.618, tol_admm=1e-4, max_admm=5000, inner_tol_mode=0,
+                              precision=prec, max_pcg=2000)
+            prob.admm_solve(o, ybar, **bounds, allow_noconv=True)  # warm-up (tables, first-use allocations)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = prob.admm_solve(o, ybar, **bounds, allow_noconv=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            s = r["stats"]
+            it = prob.iterates()
+            hx = 1.0 / (n + 1)
+            w = torch.ones(n, n, n, dtype=torch.float64, device=dev)
+            w[-1] = 0.5
+            w = w.view(-1)
+            d = it["y"] - ybar
+            misfit = math.sqrt(hx ** 3 * float(torch.sum(w * d * d)))
+            btp = prob.matvec(it["p"], F.FDE_OP_BT)
+            psi = prob.psi
+            dual_y = float((w * d + btp + it["wy"]).abs().max())
+            dual_u = float((1e-4 * w * it["u"] + psi * it["p"] + psi * it["wu"]).abs().max())
+            row[name] = {"status": r["status"], "admm": s["admm_iters"],
+                         "pcg_avg": s["pcg_iters"] / max(1, s["admm_iters"]), "E_L2": misfit,
+                         "dual_inf": max(dual_y, dual_u), "time_s": dt,
+                         "residuals": [s["res_eq"], s["res_y"], s["res_u"]]}
+        prob.close()
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"workload": "paper Table 5 sweep", "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -750,6 +815,8 @@ def main():
         run_kernels(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "paper-table5":
+        run_paper_table5(args)
     else:
         run_ours(args)
 

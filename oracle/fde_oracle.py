@@ -860,3 +860,28 @@ def active_set_solve(inst, max_iter: int = 50) -> KktSolution:
         sets = new
         sol = kkt_solve(inst, ay_lo, ay_hi, au_lo, au_hi, B=B)
     return sol
+
+
+def equality_constrained_solve(inst, tol: float = 1e-12, max_iter: int = 5000) -> KktSolution:
+    """Exact optimum of the problem without box constraints (Eq. (discretized generic
+    inverse problem) with only B y + psi u = psi g), for grids too large for the
+    dense kkt_solve. Stationarity gives y = ybar - J1^-1 B^T p and
+    u = -psi J2^-1 p, and the constraint then reads
+    (B J1^-1 B^T + psi^2 J2^-1) p = B ybar - psi g, an SPD system solved by
+    preconditioned CG (the pcg above) with the FFT-diagonal stand-in
+    |Lambda|^2 + psi^2/gamma of the multilevel circulant approximation (J1 ~ I)."""
+    p = inst.params
+    psi = psi_scale(p)
+    w = objective_weights(p)
+    g = np.zeros((p.nt, p.nx, p.ny)) if inst.g is None else inst.g
+    lt, lx, ly = preconditioner_axis_eigenvalues(p)
+    lam = psi * (lt[:, None, None] - lx[None, :, None] - ly[None, None, :])
+    sig = np.abs(lam) ** 2 + psi * psi / p.gamma
+    A = lambda v: apply_B(p, apply_B(p, v, transpose=True) / w) + (psi * psi / p.gamma) * v / w
+    M = lambda r: np.fft.ifftn(np.fft.fftn(r) / sig).real
+    rhs = apply_B(p, inst.ybar) - psi * g
+    pv, _ = pcg(A, M, rhs, np.zeros_like(rhs), tol, max_iter)
+    y = inst.ybar - apply_B(p, pv, transpose=True) / w
+    u = -psi * pv / (p.gamma * w)
+    zero = np.zeros_like(y)
+    return KktSolution(y, u, pv, zero, zero, objective(p, inst.ybar, y, u))

@@ -828,6 +828,9 @@ static int admm_solve_impl(fde_problem* P, const fde_admm_opts* o, const double*
     for (int i : {V_Y, V_U, V_ZY, V_ZU, V_P, V_WY, V_WU, V_BY}) CK(fill<double>(P->v64[i], 0.0, N, st));
   }
   P->state_valid = false;  // set again once this solve has left a consistent state
+  // a failed earlier call may have left its error flag set; the mixed sub-solve reads
+  // the flag before its PCG clears it
+  RK(clear_flag(P, st));
 
   fde_admm_stats S{};
   SolveInfo info;
