@@ -130,6 +130,9 @@ typedef struct fde_admm_opts {
                                 w_u) the previous fde_admm_solve on this problem ended with, instead
                                 of zero (FDE_EINVAL if there is none); the options and the data
                                 may differ between the calls. Batches: FDE_EUNSUPPORTED.          */
+  int inner_x0;              /* initial guess of each sub-solve: 0 the previous ADMM iterate (PCG:
+                                y^j; MINRES: (y^j, u^j, p^j)); 1 zero, as MATLAB's pcg does by
+                                default (the paper's runs, Section 6.1). fde_admm_solve only.     */
 } fde_admm_opts;
 
 typedef struct fde_admm_stats {

@@ -37,7 +37,7 @@ class fde_admm_opts(ctypes.Structure):
                 ("inner_tol_mode", ctypes.c_int), ("inner_tol", ctypes.c_double), ("precision", ctypes.c_int),
                 ("inner_tol_mixed", ctypes.c_double), ("max_refine", ctypes.c_int), ("algorithm", ctypes.c_int),
                 ("c_y", ctypes.c_double), ("c_u", ctypes.c_double), ("inner_solver", ctypes.c_int),
-                ("precond", ctypes.c_int), ("warm_start", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("warm_start", ctypes.c_int), ("inner_x0", ctypes.c_int)]
 
 
 class fde_admm_stats(ctypes.Structure):
@@ -179,12 +179,13 @@ class AdmmOptions:
     inner_solver: int = 0          # 0: PCG on the normal equations, 1: MINRES on the saddle-point system
     precond: int = 0               # 0: S-tilde, 1: matching approximation S-hat (circulant D-tilde)
     warm_start: bool = False       # continue from where the previous solve on the problem ended
+    inner_x0: int = 0              # sub-solve initial guess: 0 previous iterate, 1 zero (MATLAB pcg default)
 
     def c(self) -> fde_admm_opts:
         return fde_admm_opts(self.delta, self.rho, self.tol_admm, self.max_admm, int(self.fixed_iters), self.max_pcg,
                              self.inner_tol_mode, self.inner_tol, self.precision, self.inner_tol_mixed,
                              self.max_refine, self.algorithm, self.c_y, self.c_u, self.inner_solver, self.precond,
-                             int(self.warm_start))
+                             int(self.warm_start), int(self.inner_x0))
 
 
 def params_struct(p) -> fde_params:

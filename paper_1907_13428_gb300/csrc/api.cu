@@ -149,6 +149,7 @@ bool valid_opts(const fde_admm_opts* o) {
   if (o->inner_solver < 0 || o->inner_solver > 1) return false;
   if (o->precond < 0 || o->precond > 1) return false;
   if (o->warm_start < 0 || o->warm_start > 1) return false;
+  if (o->inner_x0 < 0 || o->inner_x0 > 1) return false;
   if (generalized(o)) return o->rho <= 1.0 && std::isfinite(o->c_y) && o->c_y >= 1.0 && std::isfinite(o->c_u);
   return true;
 }
@@ -862,10 +863,14 @@ static int admm_solve_impl(fde_problem* P, const fde_admm_opts* o, const double*
       else
         CK(apply_B<double>(P, 1, A.p, F, &omr, P->v64[V_C], &one, s64.t1, s64.t2, st));
       CK(saddle_rhs(N, P->psi, o->delta / o->rho, P->v64[V_BU], g, A.p, F + N, F + 2 * N, st));
-      // warm start from (y^j, u^j, p^j)
-      CK(cudaMemcpyAsync(X, Y, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-      CK(cudaMemcpyAsync(X + N, U, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-      CK(cudaMemcpyAsync(X + 2 * N, A.p, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+      // initial guess (y^j, u^j, p^j), or zero
+      if (o->inner_x0 == 1) {
+        CK(fill<double>(X, 0.0, 3 * N, st));
+      } else {
+        CK(cudaMemcpyAsync(X, Y, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(X + N, U, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(X + 2 * N, A.p, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+      }
       const int s = saddle_solve(P, dg, o, F, X, tol, st, &info);
       if (s != FDE_OK && s != FDE_ENOCONV) {
         status = s;
@@ -886,6 +891,10 @@ static int admm_solve_impl(fde_problem* P, const fde_admm_opts* o, const double*
       info.fp64_matvecs += 1;
     }
     bool by_valid = false;
+    if (o->inner_x0 == 1) {  // zero initial guess: y = 0 and B y = 0
+      CK(fill<double>(Y, 0.0, N, st));
+      CK(fill<double>(P->v64[V_BY], 0.0, N, st));
+    }
     const int s = subsolve(P, dg, o, P->v64[V_RHS], P->v64[V_C], P->v64[V_Q], Y, tol, st, &info, true, &by_valid);
     if (s != FDE_OK && s != FDE_ENOCONV) {
       status = s;
@@ -1304,6 +1313,7 @@ int fde_batch_admm_solve(fde_batch* b, const fde_admm_opts* o, const double* con
     if (!valid_opts_for(b->probs[i], o)) return FDE_EINVAL;
   if (o->inner_solver != 0) return FDE_EUNSUPPORTED;  // the graph solve runs PCG only
   if (o->warm_start) return FDE_EUNSUPPORTED;         // a replayed graph starts from zero
+  if (o->inner_x0) return FDE_EUNSUPPORTED;           // its sub-solves start from the previous iterate
   bool same = b->exec && std::memcmp(&b->opts, o, sizeof(*o)) == 0;
   for (int i = 0; i < n; ++i) {
     if (!ybar[i] || !y[i] || !u[i]) return FDE_EINVAL;

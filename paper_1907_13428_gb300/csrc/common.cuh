@@ -14,6 +14,15 @@ template <> struct CplxOf<double> { using type = double2; };
 template <> struct CplxOf<dd> { using type = dd2; };
 template <typename R> using cplx = typename CplxOf<R>::type;
 
+// population count on the device and on the host (index maps checked on the CPU)
+__host__ __device__ __forceinline__ int fde_popc(unsigned x) {
+#ifdef __CUDA_ARCH__
+  return __popc(x);
+#else
+  return __builtin_popcount(x);
+#endif
+}
+
 // read-only cached load
 __device__ __forceinline__ float2 ldg_(const float2* p) { return __ldg(p); }
 __device__ __forceinline__ double2 ldg_(const double2* p) { return __ldg(p); }

@@ -217,21 +217,37 @@ __host__ __device__ __forceinline__ void dftR(C* v) {
 }
 
 // One pass' arithmetic on the 16 values of thread t: butterflies q < 16/RAD,
-// j = t + T q, twiddles W_{Ns RAD}^{r (j mod Ns)} from tw = W_L^m, then DFT.
-template <typename R, int L, int RAD, bool INV, int NL, class Tab>
-__device__ __forceinline__ void rf_compute(cplx<R> (&v)[NL][16], int t, int Ns, Tab tw) {
+// j = t + T q, twiddles W_{NS RAD}^{r (j mod NS)} from tw = W_L^m, then DFT.
+// The twiddle index r (j mod NS) L/(NS RAD) splits into a per-thread part and a
+// compile-time part: for NS <= T (NS divides T) j mod NS = t mod NS for every q;
+// for NS > T the butterflies of a thread hold j = t + T q < NS, so j mod NS = j.
+template <int L, int RAD, int NS>
+struct RfTwiddle {
+  static constexpr int T = L / 16;
+  static constexpr int B = 16 / RAD;
+  static constexpr int step = L / (NS * RAD);
+  static_assert(NS <= T ? T % NS == 0 : NS >= T * B, "butterflies of one thread share j mod NS");
+  static constexpr int kq_unit = (NS <= T) ? 0 : T * step;  // compile-time part of k * step per q
+  // per-thread part of k * step
+  __host__ __device__ __forceinline__ static int thread_part(int t) {
+    return (NS <= T) ? (t & (NS - 1)) * step : t * step;
+  }
+  // index of W_L^{r k step} for butterfly q of a thread whose thread_part is kt
+  __host__ __device__ __forceinline__ static int index(int kt, int q, int r) { return r * kt + r * q * kq_unit; }
+};
+
+template <typename R, int L, int RAD, int NS, bool INV, int NL, class Tab>
+__device__ __forceinline__ void rf_compute(cplx<R> (&v)[NL][16], int t, Tab tw) {
   using C = cplx<R>;
-  constexpr int T = L / 16;
+  using TW = RfTwiddle<L, RAD, NS>;
   constexpr int B = 16 / RAD;
+  const int kt = TW::thread_part(t);
 #pragma unroll
   for (int q = 0; q < B; ++q) {
-    if (Ns > 1) {
-      const int j = t + T * q;
-      const int k = j & (Ns - 1);
-      const int step = L / (Ns * RAD);
+    if constexpr (NS > 1) {
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
-        C w = tw_get(tw, r * k * step);
+        C w = tw_get(tw, TW::index(kt, q, r));
         if (INV) w.y = -w.y;
 #pragma unroll
         for (int l = 0; l < NL; ++l) v[l][q * RAD + r] = cmul(v[l][q * RAD + r], w);
@@ -242,70 +258,154 @@ __device__ __forceinline__ void rf_compute(cplx<R> (&v)[NL][16], int t, int Ns, 
   }
 }
 
-// Shared-memory exchange: write the outputs of a pass (radix RAD, Ns), barrier,
-// read the inputs of the next pass (radix RADN), barrier. `at(l, pos)` maps a
-// line and a position to a shared-memory element.
-template <typename R, int L, int RAD, int RADN, int NL, class At>
-__device__ __forceinline__ void rf_exchange(cplx<R> (&v)[NL][16], int t, int Ns, At at) {
+// Shared-memory exchange: write the outputs of a pass (radix RAD, NS), barrier,
+// read the inputs of the next pass (radix RADN), barrier. Every position of the
+// exchange is a thread part A and a compile-time part c occupying disjoint bits
+// (write: A = (t div NS) NS RAD + t mod NS, c = T q RAD + r NS; read: A = t,
+// c = T q + r L/RADN), so a layout `Lay` maps (line l, A + c) to shared memory as
+// a per-thread base (lay.base(A), computed once) plus a constant (lay.at(b, l, c)).
+template <typename R, int L, int RAD, int RADN, int NS, int NL, class Lay>
+__device__ __forceinline__ void rf_exchange(cplx<R> (&v)[NL][16], int t, const Lay& lay) {
   constexpr int T = L / 16;
+  static_assert(T % NS == 0, "exchanges run with NS dividing T");
+  {
+    const auto b = lay.base((t / NS) * NS * RAD + (t & (NS - 1)));
 #pragma unroll
-  for (int q = 0; q < 16 / RAD; ++q) {
-    const int j = t + T * q;
-    const int base = (j / Ns) * Ns * RAD + (j & (Ns - 1));
+    for (int q = 0; q < 16 / RAD; ++q)
 #pragma unroll
-    for (int r = 0; r < RAD; ++r)
+      for (int r = 0; r < RAD; ++r)
 #pragma unroll
-      for (int l = 0; l < NL; ++l) at(l, base + r * Ns) = v[l][q * RAD + r];
+        for (int l = 0; l < NL; ++l) lay.at(b, l, T * q * RAD + r * NS) = v[l][q * RAD + r];
   }
   __syncthreads();
+  {
+    const auto b = lay.base(t);
 #pragma unroll
-  for (int q = 0; q < 16 / RADN; ++q) {
-    const int j = t + T * q;
+    for (int q = 0; q < 16 / RADN; ++q)
 #pragma unroll
-    for (int r = 0; r < RADN; ++r)
+      for (int r = 0; r < RADN; ++r)
 #pragma unroll
-      for (int l = 0; l < NL; ++l) v[l][q * RADN + r] = at(l, j + r * (L / RADN));
+        for (int l = 0; l < NL; ++l) v[l][q * RADN + r] = lay.at(b, l, T * q + r * (L / RADN));
   }
   __syncthreads();
 }
 
 // Forward transform: positions t + r T  ->  t + T q + r L/RL.
-template <typename R, int L, int NL, class At, class Tab>
-__device__ __forceinline__ void rf_forward(cplx<R> (&v)[NL][16], int t, Tab tw, At at) {
+template <typename R, int L, int NL, class Lay, class Tab>
+__device__ __forceinline__ void rf_forward(cplx<R> (&v)[NL][16], int t, Tab tw, const Lay& lay) {
   using S = RfShape<L>;
   if constexpr (S::P == 1) {
-    rf_compute<R, L, 16, false, NL>(v, t, 1, tw);
+    rf_compute<R, L, 16, 1, false, NL>(v, t, tw);
   } else if constexpr (S::P == 2) {
-    rf_compute<R, L, 16, false, NL>(v, t, 1, tw);
-    rf_exchange<R, L, 16, S::RL, NL>(v, t, 1, at);
-    rf_compute<R, L, S::RL, false, NL>(v, t, 16, tw);
+    rf_compute<R, L, 16, 1, false, NL>(v, t, tw);
+    rf_exchange<R, L, 16, S::RL, 1, NL>(v, t, lay);
+    rf_compute<R, L, S::RL, 16, false, NL>(v, t, tw);
   } else {
-    rf_compute<R, L, 16, false, NL>(v, t, 1, tw);
-    rf_exchange<R, L, 16, 16, NL>(v, t, 1, at);
-    rf_compute<R, L, 16, false, NL>(v, t, 16, tw);
-    rf_exchange<R, L, 16, S::RL, NL>(v, t, 16, at);
-    rf_compute<R, L, S::RL, false, NL>(v, t, 256, tw);
+    rf_compute<R, L, 16, 1, false, NL>(v, t, tw);
+    rf_exchange<R, L, 16, 16, 1, NL>(v, t, lay);
+    rf_compute<R, L, 16, 16, false, NL>(v, t, tw);
+    rf_exchange<R, L, 16, S::RL, 16, NL>(v, t, lay);
+    rf_compute<R, L, S::RL, 256, false, NL>(v, t, tw);
   }
 }
 
 // Inverse (unnormalised) transform: positions t + T q + r L/RL  ->  t + r T.
-template <typename R, int L, int NL, class At, class Tab>
-__device__ __forceinline__ void rf_inverse(cplx<R> (&v)[NL][16], int t, Tab tw, At at) {
+template <typename R, int L, int NL, class Lay, class Tab>
+__device__ __forceinline__ void rf_inverse(cplx<R> (&v)[NL][16], int t, Tab tw, const Lay& lay) {
   using S = RfShape<L>;
   if constexpr (S::P == 1) {
-    rf_compute<R, L, 16, true, NL>(v, t, 1, tw);
+    rf_compute<R, L, 16, 1, true, NL>(v, t, tw);
   } else if constexpr (S::P == 2) {
-    rf_compute<R, L, S::RL, true, NL>(v, t, 1, tw);
-    rf_exchange<R, L, S::RL, 16, NL>(v, t, 1, at);
-    rf_compute<R, L, 16, true, NL>(v, t, S::RL, tw);
+    rf_compute<R, L, S::RL, 1, true, NL>(v, t, tw);
+    rf_exchange<R, L, S::RL, 16, 1, NL>(v, t, lay);
+    rf_compute<R, L, 16, S::RL, true, NL>(v, t, tw);
   } else {
-    rf_compute<R, L, S::RL, true, NL>(v, t, 1, tw);
-    rf_exchange<R, L, S::RL, 16, NL>(v, t, 1, at);
-    rf_compute<R, L, 16, true, NL>(v, t, S::RL, tw);
-    rf_exchange<R, L, 16, 16, NL>(v, t, S::RL, at);
-    rf_compute<R, L, 16, true, NL>(v, t, 16 * S::RL, tw);
+    rf_compute<R, L, S::RL, 1, true, NL>(v, t, tw);
+    rf_exchange<R, L, S::RL, 16, 1, NL>(v, t, lay);
+    rf_compute<R, L, 16, S::RL, true, NL>(v, t, tw);
+    rf_exchange<R, L, 16, 16, S::RL, NL>(v, t, lay);
+    rf_compute<R, L, 16, 16 * S::RL, true, NL>(v, t, tw);
   }
 }
+
+// ---------------------------------------------------------------------------
+// Shared-memory layouts of the exchanges. base(A) returns two element pointers;
+// at(b, l, c) picks one by a compile-time selector of (l, c) and adds a
+// compile-time offset, which is valid because A and c have disjoint bits.
+// ---------------------------------------------------------------------------
+
+// Line-major with one pad element per 16 positions: element (l, pos) at
+// line0 + l*LS + pos + pos/16 (conflict-free for the Stockham strides).
+// Bases are 32-bit element offsets (one register each).
+template <typename C, int LS>
+struct PadLayout {
+  C* line0;
+  struct Base { int o; };
+  __host__ __device__ __forceinline__ Base base(int A) const { return {A + (A >> 4)}; }
+  __host__ __device__ __forceinline__ C& at(const Base& b, int l, int c) const {
+    return line0[b.o + l * LS + c + (c >> 4)];
+  }
+};
+
+// Position-major, 2 CP lines per position row (line l of column pair cl at
+// l*CP + cl), the line index XOR-swizzled by CP when the low five position bits
+// have odd parity: element (l, pos) at pos*LW + ((l*CP + cl) ^ (par(pos & 31) CP)).
+// With par(A + c) = par(A) ^ par(c) the swizzle picks one of two per-thread bases.
+template <typename C, int CP>
+struct SwizzleLayout {
+  C* sm;
+  int cl;
+  struct Base { int o[2]; };
+  static constexpr int LW = 2 * CP;
+  __host__ __device__ __forceinline__ Base base(int A) const {
+    const int pa = fde_popc(A & 31) & 1;
+    const int row = A * LW + cl;
+    return {{row + CP * pa, row + CP * (pa ^ 1)}};
+  }
+  __host__ __device__ __forceinline__ C& at(const Base& b, int l, int c) const {
+    const int k = (l ^ fde_popc(c & 31)) & 1;
+    return sm[b.o[k] + c * LW];
+  }
+};
+
+// SwizzleLayout with the line fixed at run time (the split-halves kernels: the
+// thread group h owns line h): the selector becomes h ^ par(c).
+template <typename C, int CP>
+struct SwizzleLineLayout {
+  C* sm;
+  int cl, h;
+  struct Base { int o[2]; };
+  static constexpr int LW = 2 * CP;
+  __host__ __device__ __forceinline__ Base base(int A) const {
+    const int pa = fde_popc(A & 31) & 1;
+    const int row = A * LW + cl;
+    return {{row + CP * (pa ^ h), row + CP * (pa ^ h ^ 1)}};
+  }
+  __host__ __device__ __forceinline__ C& at(const Base& b, int, int c) const {
+    return sm[b.o[fde_popc(c & 31) & 1] + c * LW];
+  }
+};
+
+// Position-major, CP columns per position row, the physical row pos with bit 0
+// flipped when position bits 1..4 have odd parity: element pos at
+// (pos ^ par(pos & 30)) * CP + cl. Writing A + c = (A & ~1) + (c & ~1) + (A0 ^ c0)
+// gives phys = (A & ~1) + (c & ~1) + (u ^ k), u = A0 ^ par(A & 30) per thread and
+// k = c0 ^ par(c & 30) at compile time.
+template <typename C, int CP>
+struct FlipLayout {
+  C* sm;
+  int cl;
+  struct Base { int o[2]; };
+  __host__ __device__ __forceinline__ Base base(int A) const {
+    const int u = (A & 1) ^ (fde_popc(A & 30) & 1);
+    const int row = (A & ~1) * CP + cl;
+    return {{row + CP * u, row + CP * (u ^ 1)}};
+  }
+  __host__ __device__ __forceinline__ C& at(const Base& b, int, int c) const {
+    const int k = (c & 1) ^ (fde_popc(c & 30) & 1);
+    return sm[b.o[k] + (c & ~1) * CP];
+  }
+};
 
 // Frequency position held in v[.][q RL + r] after rf_forward.
 template <int L>

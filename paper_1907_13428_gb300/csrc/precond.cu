@@ -326,10 +326,7 @@ __global__ void __launch_bounds__(NT) k_prec_axis_reg(cplx<R>* __restrict__ spec
   const long long o = valid ? q / n_inner : 0;
   const long long c = valid ? q - o * n_inner : 0;
   const long long base = o * outer_stride + c;
-  auto at = [sm, cl](int, int pos) -> C& {
-    const int phys = pos ^ (__popc(pos & 30) & 1);
-    return sm[phys * CP + cl];
-  };
+  const FlipLayout<C, CP> lay{sm, cl};
   C v[1][16];
   if (mode == 1) {
 #pragma unroll
@@ -337,14 +334,14 @@ __global__ void __launch_bounds__(NT) k_prec_axis_reg(cplx<R>* __restrict__ spec
       const int p = rf_freq<L>(t, idx);
       v[0][idx] = valid ? spec[base + p * axis_stride] : mk<C>(0, 0);
     }
-    rf_inverse<R, L, 1>(v, t, twn, at);
+    rf_inverse<R, L, 1>(v, t, twn, lay);
   } else {
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int p = t + r * T;
       v[0][r] = valid ? spec[base + p * axis_stride] : mk<C>(0, 0);
     }
-    rf_forward<R, L, 1>(v, t, twn, at);
+    rf_forward<R, L, 1>(v, t, twn, lay);
     if (mode == 2) {
       const int i = (int)(c / dv.Hp), j = (int)(c - (long long)i * dv.Hp);
       const bool pad = j >= dv.H;
@@ -363,7 +360,7 @@ __global__ void __launch_bounds__(NT) k_prec_axis_reg(cplx<R>* __restrict__ spec
         const R sc = pad ? (R)0 : (R)dv.inv_N / sigma;
         v[0][idx] = cscale(v[0][idx], sc);
       }
-      rf_inverse<R, L, 1>(v, t, twn, at);
+      rf_inverse<R, L, 1>(v, t, twn, lay);
     }
   }
   if (!valid) return;
@@ -456,13 +453,14 @@ __global__ void __launch_bounds__(NT) k_prec_rows_fwd_reg(const R* __restrict__ 
   const long long ra = ((long long)blockIdx.x * PAIRS + pr) * 2, rb = ra + 1;
   C* my = sm + pr * LS;
   auto at = [my](int, int pos) -> C& { return my[pos + (pos >> 4)]; };
+  const PadLayout<C, LS> lay{my};
   C v[1][16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
     const int p = t + q * T;
     v[0][q] = mk<C>(ra < nrows ? r[ra * L + p] : (R)0, rb < nrows ? r[rb * L + p] : (R)0);
   }
-  rf_forward<R, L, 1>(v, t, twn, at);
+  rf_forward<R, L, 1>(v, t, twn, lay);
 #pragma unroll
   for (int idx = 0; idx < 16; ++idx) at(0, rf_freq<L>(t, idx)) = v[0][idx];
   __syncthreads();
@@ -492,7 +490,7 @@ __global__ void __launch_bounds__(NT) k_prec_rows_inv_reg(const cplx<R>* __restr
   const int pr = threadIdx.x / T, t = threadIdx.x - pr * T;
   const long long ra = ((long long)blockIdx.x * PAIRS + pr) * 2, rb = ra + 1;
   C* my = sm + pr * LS;
-  auto at = [my](int, int pos) -> C& { return my[pos + (pos >> 4)]; };
+  const PadLayout<C, LS> lay{my};
   C v[1][16];
 #pragma unroll
   for (int idx = 0; idx < 16; ++idx) {
@@ -507,7 +505,7 @@ __global__ void __launch_bounds__(NT) k_prec_rows_inv_reg(const cplx<R>* __restr
     }
     v[0][idx] = mk<C>(A.x - B.y, A.y + B.x);  // A + i B
   }
-  rf_inverse<R, L, 1>(v, t, twn, at);
+  rf_inverse<R, L, 1>(v, t, twn, lay);
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
     const int p = t + q * T;

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const
   const int pr = threadIdx.x / T, t = threadIdx.x - pr * T;
   const long long ra = ((long long)blockIdx.x * PAIRS + pr) * 2, rb = ra + 1;
   C* my = sm + pr * 2 * LS;
-  auto at = [my](int l, int pos) -> C& { return my[l * LS + pos + (pos >> 4)]; };
+  const PadLayout<C, LS> lay{my};
   C v[2][16];
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const
     v[0][r] = mk<C>(a, b);
     v[1][r] = (FULL || p < n) ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
   }
-  rf_forward<R, L, 2>(v, t, twL, at);
+  rf_forward<R, L, 2>(v, t, twL, lay);
 #pragma unroll
   for (int idx = 0; idx < 16; ++idx) {
     const int k = rf_freq<L>(t, idx);
@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const
       v[l][idx] = cmul(v[l][idx], w);
     }
   }
-  rf_inverse<R, L, 2>(v, t, twL, at);
+  rf_inverse<R, L, 2>(v, t, twL, lay);
   const int ta = (int)(ra / E.rows_per_slice), tb = (int)(rb / E.rows_per_slice);
   // epilogue in chunks of 4 positions: all operand loads of a chunk are issued
   // before any arithmetic or store, so their latencies overlap
@@ -101,10 +101,8 @@ __global__ void __launch_bounds__(NT) k_axis_reg(const S* __restrict__ x, int n,
   const long long c = valid ? 2 * (q - o * npi) : 0;
   const long long base = o * outer_stride + c;
   const bool has_b = valid && (c + 1 < n_inner);
-  auto at = [sm, cl](int l, int pos) -> C& {
-    const int sw = (__popc(pos & 31) & 1) ? CP : 0;
-    return sm[pos * LW + ((l * CP + cl) ^ sw)];
-  };
+  const SwizzleLayout<C, CP> lay{sm, cl};
+  static_assert(SwizzleLayout<C, CP>::LW == LW, "layout row width");
   C v[2][16];
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
@@ -124,7 +122,7 @@ __global__ void __launch_bounds__(NT) k_axis_reg(const S* __restrict__ x, int n,
     v[0][r] = mk<C>(a, b);
     v[1][r] = (FULL || p < n) ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
   }
-  rf_forward<R, L, 2>(v, t, twL, at);
+  rf_forward<R, L, 2>(v, t, twL, lay);
 #pragma unroll
   for (int idx = 0; idx < 16; ++idx) {
     const int k = rf_freq<L>(t, idx);
@@ -135,7 +133,7 @@ __global__ void __launch_bounds__(NT) k_axis_reg(const S* __restrict__ x, int n,
       v[l][idx] = cmul(v[l][idx], w);
     }
   }
-  rf_inverse<R, L, 2>(v, t, twL, at);
+  rf_inverse<R, L, 2>(v, t, twL, lay);
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
     const int p = t + r * T;
@@ -185,7 +183,7 @@ __global__ void __launch_bounds__(NT, split_min_blocks<R>(NT)) k_rows_split(cons
   const long long ra = ((long long)blockIdx.x * PAIRS + pr) * 2, rb = ra + 1;
   C* my = sm + (pr * 2 + h) * LS;
   C* other = sm + (pr * 2 + (h ^ 1)) * LS;
-  auto at = [my](int, int pos) -> C& { return my[pos + (pos >> 4)]; };
+  const PadLayout<C, LS> lay{my};
   C v[1][16];
   if constexpr (!std::is_same<R, S>::value) {
     // both groups need the whole line pair: each converts the positions of its own
@@ -227,14 +225,14 @@ __global__ void __launch_bounds__(NT, split_min_blocks<R>(NT)) k_rows_split(cons
       if (h) v[0][r] = (FULL || p < n) ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
     }
   }
-  rf_forward<R, L, 1>(v, t, twL, at);
+  rf_forward<R, L, 1>(v, t, twL, lay);
 #pragma unroll
   for (int idx = 0; idx < 16; ++idx) {
     C w = ldg_(&sym[h * L + rf_freq<L>(t, idx)]);
     if (conj_sym) w.y = -w.y;
     v[0][idx] = cmul(v[0][idx], w);
   }
-  rf_inverse<R, L, 1>(v, t, twL, at);
+  rf_inverse<R, L, 1>(v, t, twL, lay);
   // the odd half's term is v conj(tw2[p]); hand over the positions the other group finishes
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
@@ -300,7 +298,7 @@ __global__ void __launch_bounds__(NT, split_min_blocks<R>(NT)) k_axis_split(cons
     const int sw = (__popc(pos & 31) & 1) ? CP : 0;
     return pos * LW + ((l * CP + cl) ^ sw);
   };
-  auto at = [sm, h, slot](int, int pos) -> C& { return sm[slot(h, pos)]; };
+  const SwizzleLineLayout<C, CP> lay{sm, cl, h};
   C v[1][16];
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
@@ -320,14 +318,14 @@ __global__ void __launch_bounds__(NT, split_min_blocks<R>(NT)) k_axis_split(cons
     v[0][r] = mk<C>(a, b);
     if (h) v[0][r] = (FULL || p < n) ? cmul(v[0][r], ldg_(&tw2[p])) : mk<C>(0, 0);
   }
-  rf_forward<R, L, 1>(v, t, twL, at);
+  rf_forward<R, L, 1>(v, t, twL, lay);
 #pragma unroll
   for (int idx = 0; idx < 16; ++idx) {
     C w = ldg_(&sym[h * L + rf_freq<L>(t, idx)]);
     if (conj_sym) w.y = -w.y;
     v[0][idx] = cmul(v[0][idx], w);
   }
-  rf_inverse<R, L, 1>(v, t, twL, at);
+  rf_inverse<R, L, 1>(v, t, twL, lay);
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
     const int p = t + r * T;
