@@ -69,8 +69,11 @@ enum fde_precision {
                      target: rel * inner_tol_mixed > tol), double for the others; an
                      evaluation that meets the target in double-float is repeated in
                      double. The accepted residual of every sub-problem and the B y that
-                     feeds the ADMM step are double products. Batches: every evaluation
-                     but the last in double-float, the last in double.                  */
+                     feeds the ADMM step are double products. The first evaluation of a
+                     warm-started sub-problem, which only steers the first correction,
+                     runs in float while the warm starts are far from the solutions
+                     (relative residual >= 1e-3). Batches: every evaluation but the last
+                     in double-float, the last in double.                                */
 };
 
 enum fde_op {
@@ -150,6 +153,8 @@ typedef struct fde_admm_stats {
                                 residual instead of an evaluated one                              */
   double copy_in_ms;         /* fde_admm_solve_host: device time of the host-to-device copies     */
   double copy_out_ms;        /* fde_admm_solve_host: device time of the device-to-host copies     */
+  int float_steers;          /* MIXED_DFV: first evaluations of a warm-started sub-problem run in
+                                float (they only steer the first correction; never accepted)      */
 } fde_admm_stats;
 
 typedef struct fde_problem fde_problem;
@@ -201,7 +206,7 @@ int fde_autotune(fde_problem* prob, void* stream);
 /* Current tile choice of the x2 pass and x1 pass, for precision FDE_FP32 (the
  * float passes), FDE_MIXED_DF (the double-float passes) or FDE_FP64 (the double
  * passes): threads per CTA of the kernel that holds both embedding halves of a
- * line pair in each thread (float x2: 128 or 256, x1: 256 or 512; double-float
+ * line pair in each thread (float x2: 128, 256 or 512, x1: 256 or 512; double-float
  * and double: 256), or, negated, of the double-float or double split-halves
  * kernel whose two thread groups hold one half each (x2: 256 or 512, x1: 512). */
 int fde_tiles(const fde_problem* prob, int precision, int* rows_threads, int* axis_threads);

@@ -509,10 +509,11 @@ def pcg(apply_A, apply_M, b, x0, tol, max_iter):
 
 
 def admm_pcg(inst, o: AdmmOptions, iters: Optional[int] = None, inner_tol: float = 1e-10,
-             max_pcg: int = 500, paper_inner_rule: bool = False) -> AdmmState:
+             max_pcg: int = 500, paper_inner_rule: bool = False, x0_zero: bool = False) -> AdmmState:
     """Algorithm 1 with each sub-problem solved by PCG preconditioned with S-tilde
-    (Section 6.1), warm-started from the previous y. With paper_inner_rule the PCG
-    tolerance is 0.05 max{min{residuals}, tol} (Section 6.1); else inner_tol."""
+    (Section 6.1), warm-started from the previous y (x0_zero: from zero, the default
+    initial guess of MATLAB's pcg). With paper_inner_rule the PCG tolerance is
+    0.05 max{min{residuals}, tol} (Section 6.1); else inner_tol."""
     p = inst.params
     g = np.zeros((p.nt, p.nx, p.ny)) if inst.g is None else inst.g
     lo_y, hi_y = box_bounds(p, inst.ya, inst.yb)
@@ -527,7 +528,7 @@ def admm_pcg(inst, o: AdmmOptions, iters: Optional[int] = None, inner_tol: float
             tol = 0.05 * max(min(st.residuals), o.tol) if st.iters > 0 else 0.05
         else:
             tol = inner_tol
-        y, k = pcg(A, M, rhs, st.y, tol, max_pcg)
+        y, k = pcg(A, M, rhs, np.zeros_like(st.y) if x0_zero else st.y, tol, max_pcg)
         pcg_hist = st.pcg_iters + [k]
         st = admm_after_solve(p, o, g, lo_y, hi_y, lo_u, hi_u, st, y, bu, r0)
         st.pcg_iters = pcg_hist

@@ -45,7 +45,7 @@ class fde_admm_stats(ctypes.Structure):
                 ("fp64_matvecs", ctypes.c_int), ("res_eq", ctypes.c_double), ("res_y", ctypes.c_double),
                 ("res_u", ctypes.c_double), ("objective", ctypes.c_double), ("max_sub_relres", ctypes.c_double),
                 ("recursive_steers", ctypes.c_int), ("copy_in_ms", ctypes.c_double),
-                ("copy_out_ms", ctypes.c_double)]
+                ("copy_out_ms", ctypes.c_double), ("float_steers", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -260,7 +260,7 @@ int op_M(fde_problem* P, const Diags& dg, const R* r, R* z, cudaStream_t st, Gat
 }
 
 struct SolveInfo {
-  int pcg_iters = 0, refine = 0, fp64_matvecs = 0, recursive = 0;
+  int pcg_iters = 0, refine = 0, fp64_matvecs = 0, recursive = 0, float_steers = 0;
   double relres = 0.0;
 };
 
@@ -320,6 +320,15 @@ int subsolve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const doub
   // own error, is about kFloatDrift of the residual the correction started from, so a start
   // residual rel with rel * kFloatDrift <= tol / 10 skips one evaluation (two products).
   constexpr double kFloatDrift = 1e-6;
+  // FDE_MIXED_DFV: the first evaluation of a warm-started sub-problem only steers the
+  // first correction. When the previous sub-problem started far from its solution
+  // (relative residual >= kFloatSteer) it runs in float: the folded halves are formed in
+  // double and rounded, B^T runs in float, and the result, accurate to about 1e-7 of
+  // ||rhs||, is the correction's right-hand side as it stands. It is used when its own
+  // relative residual is >= kFloatSteer / 10 (a thousand times its rounding error);
+  // otherwise the evaluation is repeated in double-float. It is never accepted.
+  constexpr double kFloatSteer = 1e-3;
+  const bool steer32 = dfv && by_on_entry && P->last_rel0 >= kFloatSteer && maxref > 0;
   bool implicit_next = false;
   double rel_implicit = 0.0;
   for (int k = 0; k <= maxref; ++k) {
@@ -327,7 +336,27 @@ int subsolve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const doub
     const bool had_implicit = implicit_next;
     implicit_next = false;
     const bool implicit = had_implicit && rel_implicit > tol && k < maxref;
-    if (implicit) {
+    bool used32 = false;
+    if (k == 0 && steer32) {
+      CK(fold(P->v64[V_BY], q, c, y, dg.M2inv.v, dg.M1.v, last, N, P->v64[V_SD], P->v64[V_Z], st));
+      CK(to_f32(P->v64[V_SD], P->v32[F_D], N, st));
+      CK(to_f32(P->v64[V_Z], P->v32[F_R], N, st));
+      CK(apply_B<float>(P, 1, P->v32[F_D], P->v32[F_B], nullptr, P->v32[F_R], &one, s32.t1, s32.t2, st));
+      CK((dot<float, float>(P, P->v32[F_B], P->v32[F_B], N, S_RR, FIN_STORE, st)));
+      flag = read_scalars(P, st);
+      if (flag < 0) return flag;
+      rel = std::sqrt(P->hscal[S_RR] / bb);
+      if (rel >= 0.1 * kFloatSteer) {
+        used32 = true;
+        P->last_rel0 = rel;
+        info->float_steers += 1;
+        info->relres = rel;
+        dd = rel * inner > tol;
+      }
+    }
+    if (used32) {
+      // F_B holds the float residual: straight to the correction
+    } else if (implicit) {
       rel = rel_implicit;
       CK(copy<float>(P->v32[F_B], P->v32[F_R], N, st));  // the recursive residual is the next right-hand side
       dd = rel * inner > tol;
@@ -356,6 +385,7 @@ int subsolve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const doub
       }
       rel_implicit = 0.0;
       info->relres = rel;
+      if (k == 0) P->last_rel0 = rel;
       if (rel <= tol) return FDE_OK;
       if (k == maxref) break;
       if (dfv) dd = rel * inner > tol;
@@ -371,7 +401,7 @@ int subsolve(fde_problem* P, const Diags& dg, const fde_admm_opts* o, const doub
     if (s != FDE_OK && s != FDE_ENOCONV) return s;
     CK(add_f32(y, P->v32[F_X], N, st));
     *by_valid = false;
-    if (dfv && !implicit && rel * kFloatDrift <= 0.1 * tol) {
+    if (dfv && !implicit && !used32 && rel * kFloatDrift <= 0.1 * tol) {
       implicit_next = true;
       rel_implicit = rr32 * rel;  // |r - S d| / |rhs| from the PCG's own residual
     }
@@ -749,7 +779,7 @@ int fde_set_tiles(fde_problem* P, int precision, int rows_threads, int axis_thre
   const bool long_rows = P->ax[2].L > 2048;
   bool rows_ok, axis_ok;
   if (precision == FDE_FP32) {
-    rows_ok = rows_threads == 0 || rows_threads == 256 || (!long_rows && rows_threads == 128);
+    rows_ok = rows_threads == 0 || rows_threads == 256 || rows_threads == 512 || (!long_rows && rows_threads == 128);
     axis_ok = axis_threads == 0 || axis_threads == 512 || axis_threads == 256;
   } else {
     rows_ok = rows_threads == 0 || rows_threads == 256 || rows_threads == -512 || (!long_rows && rows_threads == -256);
@@ -827,6 +857,7 @@ static int admm_solve_impl(fde_problem* P, const fde_admm_opts* o, const double*
     if (!P->state_valid) return FDE_EINVAL;
   } else {
     for (int i : {V_Y, V_U, V_ZY, V_ZU, V_P, V_WY, V_WU, V_BY}) CK(fill<double>(P->v64[i], 0.0, N, st));
+    P->last_rel0 = 1.0;
   }
   P->state_valid = false;  // set again once this solve has left a consistent state
   // a failed earlier call may have left its error flag set; the mixed sub-solve reads
@@ -930,6 +961,7 @@ static int admm_solve_impl(fde_problem* P, const fde_admm_opts* o, const double*
   S.pcg_iters = info.pcg_iters;
   S.refine_steps = info.refine;
   S.recursive_steers = info.recursive;
+  S.float_steers = info.float_steers;
   S.fp64_matvecs = info.fp64_matvecs;
   S.res_eq = res[0];
   S.res_y = res[1];
@@ -1050,6 +1082,7 @@ int fde_admm_set_iterates(fde_problem* P, const double* y, const double* u, cons
   auto s = scratch64(P);
   CK(apply_B<double>(P, 0, P->v64[V_Y], P->v64[V_BY], nullptr, nullptr, nullptr, s.t1, s.t2, st));
   CK(cudaStreamSynchronize(st));
+  P->last_rel0 = 1.0;
   P->state_valid = true;
   return FDE_OK;
 }

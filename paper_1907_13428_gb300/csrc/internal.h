@@ -76,7 +76,7 @@ struct fde_problem {
   void* allocs[128] = {};
   int nallocs = 0;
   // FFT tile choice of the float register kernels (threads per CTA), set by fde_autotune
-  int rows_nt32 = 256;  // x2 pass: 128 or 256 (row pairs per CTA = threads / (L/16))
+  int rows_nt32 = 256;  // x2 pass: 128, 256 or 512 (row pairs per CTA = threads / (L/16))
   int axis_nt32 = 512;  // x1 / t pass: 256 or 512 (column pairs per CTA = threads / (L/16))
   // negative values: the split-halves kernels with that many threads
   // tile choice of the double-float passes: 256 (both halves per thread) or split (-256/-512 x2, -512 x1)
@@ -86,6 +86,7 @@ struct fde_problem {
   int rows_nt64 = 256;
   int axis_nt64 = 256;
   bool state_valid = false;  // the ADMM iterates hold the end of a previous solve (warm start)
+  double last_rel0 = 1.0;    // relative residual of the previous sub-problem's warm start (FDE_MIXED_DFV)
 };
 
 namespace fde {

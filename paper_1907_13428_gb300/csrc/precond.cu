@@ -308,12 +308,22 @@ cudaError_t precond_set_smem_attrs() {
 
 namespace fde {
 
-template <typename R, int L, int NT>
-__global__ void __launch_bounds__(NT) k_prec_axis_reg(cplx<R>* __restrict__ spec, long long axis_stride,
-                                                       long long n_inner, long long outer_stride, long long n_outer,
-                                                       const cplx<R>* __restrict__ twn, int mode, DivArgs dv,
-                                                       const cplx<R>* __restrict__ lt, const cplx<R>* __restrict__ lx,
-                                                       const cplx<R>* __restrict__ ly) {
+// Plain transforms (modes 0, 1) are compiled for two resident CTAs (at most 64
+// registers a thread with 512 threads): they move the whole spectrum through HBM
+// and need the warps to hide its latency; the divide pass keeps one CTA.
+template <int MODE> constexpr int prec_min_blocks() { return MODE == 2 ? 1 : 2; }
+
+// 1/sigma: the float pass uses the fast reciprocal (a preconditioner needs no
+// correctly rounded quotient), the double pass the IEEE quotient.
+__device__ __forceinline__ float prec_recip(float s) { return __frcp_rn(s); }
+__device__ __forceinline__ double prec_recip(double s) { return 1.0 / s; }
+
+template <typename R, int L, int NT, int MODE>
+__global__ void __launch_bounds__(NT, prec_min_blocks<MODE>()) k_prec_axis_reg(
+    cplx<R>* __restrict__ spec, long long axis_stride, long long n_inner, long long outer_stride, long long n_outer,
+    const cplx<R>* __restrict__ twn, DivArgs dv, const cplx<R>* __restrict__ lt, const cplx<R>* __restrict__ lx,
+    const cplx<R>* __restrict__ ly) {
+  constexpr int mode = MODE;
   if (gate_closed(dv.gate)) return;
   using C = cplx<R>;
   constexpr int T = L / 16, CP = NT / T;
@@ -328,7 +338,7 @@ __global__ void __launch_bounds__(NT) k_prec_axis_reg(cplx<R>* __restrict__ spec
   const long long base = o * outer_stride + c;
   const FlipLayout<C, CP> lay{sm, cl};
   C v[1][16];
-  if (mode == 1) {
+  if constexpr (mode == 1) {
 #pragma unroll
     for (int idx = 0; idx < 16; ++idx) {
       const int p = rf_freq<L>(t, idx);
@@ -342,7 +352,7 @@ __global__ void __launch_bounds__(NT) k_prec_axis_reg(cplx<R>* __restrict__ spec
       v[0][r] = valid ? spec[base + p * axis_stride] : mk<C>(0, 0);
     }
     rf_forward<R, L, 1>(v, t, twn, lay);
-    if (mode == 2) {
+    if constexpr (mode == 2) {
       const int i = (int)(c / dv.Hp), j = (int)(c - (long long)i * dv.Hp);
       const bool pad = j >= dv.H;
       const C b = pad ? mk<C>(0, 0) : __ldg(&lx[i]);
@@ -357,14 +367,14 @@ __global__ void __launch_bounds__(NT) k_prec_axis_reg(cplx<R>* __restrict__ spec
         const R li = (R)dv.psi * (a.y - b.y - d.y);
         const R mag = lr * lr + li * li;
         const R sigma = dv.adjoint ? mag : (R)dv.m1 + mag * (R)dv.inv_m2 + (R)dv.cre * lr;
-        const R sc = pad ? (R)0 : (R)dv.inv_N / sigma;
+        const R sc = pad ? (R)0 : (R)dv.inv_N * prec_recip(sigma);
         v[0][idx] = cscale(v[0][idx], sc);
       }
       rf_inverse<R, L, 1>(v, t, twn, lay);
     }
   }
   if (!valid) return;
-  if (mode == 0) {
+  if constexpr (mode == 0) {
 #pragma unroll
     for (int idx = 0; idx < 16; ++idx) spec[base + rf_freq<L>(t, idx) * axis_stride] = v[0][idx];
   } else {
@@ -385,8 +395,15 @@ static cudaError_t launch_prec_axis_reg_L(cplx<R>* spec, long long axis_stride, 
   const long long total = n_outer * n_inner;
   const long long grid = (total + CP - 1) / CP;
   const size_t smem = (size_t)L * CP * sizeof(cplx<R>);
-  k_prec_axis_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(spec, axis_stride, n_inner, outer_stride, n_outer,
-                                                              twn, mode, dv, lt, lx, ly);
+  if (mode == 0)
+    k_prec_axis_reg<R, L, NT, 0><<<(unsigned)grid, NT, smem, st>>>(spec, axis_stride, n_inner, outer_stride, n_outer,
+                                                                   twn, dv, lt, lx, ly);
+  else if (mode == 1)
+    k_prec_axis_reg<R, L, NT, 1><<<(unsigned)grid, NT, smem, st>>>(spec, axis_stride, n_inner, outer_stride, n_outer,
+                                                                   twn, dv, lt, lx, ly);
+  else
+    k_prec_axis_reg<R, L, NT, 2><<<(unsigned)grid, NT, smem, st>>>(spec, axis_stride, n_inner, outer_stride, n_outer,
+                                                                   twn, dv, lt, lx, ly);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -419,15 +436,17 @@ template cudaError_t launch_prec_axis_reg<double>(int, double2*, long long, long
 cudaError_t precond_reg_set_smem_attrs() {
   const int big = 200 * 1024;
   cudaError_t e = cudaSuccess;
-#define FDE_ATTR(LL)                                                                              \
+#define FDE_ATTR1(LL, M)                                                                          \
   if (e == cudaSuccess)                                                                           \
-    e = cudaFuncSetAttribute(k_prec_axis_reg<float, LL, prec_nt<float>()>,                        \
+    e = cudaFuncSetAttribute(k_prec_axis_reg<float, LL, prec_nt<float>(), M>,                     \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, big);                   \
   if (e == cudaSuccess)                                                                           \
-    e = cudaFuncSetAttribute(k_prec_axis_reg<double, LL, prec_nt<double>()>,                      \
+    e = cudaFuncSetAttribute(k_prec_axis_reg<double, LL, prec_nt<double>(), M>,                   \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+#define FDE_ATTR(LL) FDE_ATTR1(LL, 0) FDE_ATTR1(LL, 1) FDE_ATTR1(LL, 2)
   FDE_FOR_EACH_PL(FDE_ATTR)
 #undef FDE_ATTR
+#undef FDE_ATTR1
   return e;
 }
 
@@ -565,6 +584,7 @@ cudaError_t precond_rows_reg_set_smem_attrs() {
                              big);
   FDE_FOR_EACH_PL(FDE_ATTR)
 #undef FDE_ATTR
+#undef FDE_ATTR1
   return e;
 }
 

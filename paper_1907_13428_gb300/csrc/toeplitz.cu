@@ -409,11 +409,11 @@ cudaError_t autotune_tiles(fde_problem* P, const float* x, float* y, const doubl
     *field = pick;
     return cudaSuccess;
   };
-  const int rows32[2] = {256, 128};
+  const int rows32[3] = {256, 128, 512};
   const int axis32[2] = {512, 256};
   const int rows64[3] = {256, -512, -256};
   const int axis64[2] = {256, -512};
-  if (e == cudaSuccess) e = tune(&P->rows_nt32, rows32, 2, 2, 0, true);
+  if (e == cudaSuccess) e = tune(&P->rows_nt32, rows32, 3, 2, 0, true);
   if (e == cudaSuccess) e = tune(&P->axis_nt32, axis32, 2, 1, 0, false);
   if (e == cudaSuccess) e = tune(&P->rows_ntdd, rows64, 3, 2, 1, true);
   if (e == cudaSuccess) e = tune(&P->axis_ntdd, axis64, 2, 1, 1, false);

@@ -13,8 +13,12 @@ namespace fde {
 // R: arithmetic of the transforms; S: storage type of the vectors (R, or double
 // for double-float arithmetic).
 // FULL: the lines fill the transform (n == L), so no position is out of range.
+// Resident CTAs per SM the x2 pass is compiled for: float tiles of up to 256
+// threads run two CTAs (128 registers for 256 threads), the 512-thread tile one.
+template <typename R> constexpr int rows_min_blocks(int nt) { return sizeof(R) == 4 && nt < 512 ? 2 : 1; }
+
 template <typename R, int L, int NT, typename S = R, bool FULL = false>
-__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 2 : 1)) k_rows_reg(const S* __restrict__ x, long long nrows,
+__global__ void __launch_bounds__(NT, rows_min_blocks<R>(NT)) k_rows_reg(const S* __restrict__ x, long long nrows,
                                                   int n, const cplx<R>* __restrict__ sym,
                                                   const cplx<R>* __restrict__ tw2, const cplx<R>* __restrict__ twL,
                                                   int conj_sym, AxisEpi<S> E) {
@@ -392,7 +396,7 @@ static cudaError_t launch_rows_split_LN(fde_problem* P, const S* x, int conj_sym
   return cudaGetLastError();
 }
 
-// The tile chosen by fde_autotune: float 128 or 256 threads; double and
+// The tile chosen by fde_autotune: float 128, 256 or 512 threads; double and
 // double-float 256 threads, or the split-halves variant with 256 or 512 threads
 // (stored negated).
 template <typename R, int L, typename S>
@@ -402,6 +406,7 @@ cudaError_t launch_rows_reg_L(fde_problem* P, const S* x, int conj_sym, const cp
     if constexpr (L <= 2048) {
       if (P->rows_nt32 == 128) return launch_rows_reg_LN<R, L, 128, S>(P, x, conj_sym, sym, T, E, st);
     }
+    if (P->rows_nt32 == 512) return launch_rows_reg_LN<R, L, 512, S>(P, x, conj_sym, sym, T, E, st);
   }
   if constexpr (!std::is_same<R, float>::value) {
     const int choice = std::is_same<R, dd>::value ? P->rows_ntdd : P->rows_nt64;
@@ -528,6 +533,7 @@ cudaError_t reg_attrs_L() {
   if constexpr (std::is_same<R, float>::value) {
     smem_attr(e, k_axis_reg<R, L, 256, S, false>, k_axis_reg<R, L, 256, S, true>);
     if constexpr (L <= 2048) smem_attr(e, k_rows_reg<R, L, 128, S, false>, k_rows_reg<R, L, 128, S, true>);
+    smem_attr(e, k_rows_reg<R, L, 512, S, false>, k_rows_reg<R, L, 512, S, true>);
   }
   if constexpr (!std::is_same<R, float>::value) {
     smem_attr(e, k_rows_split<R, L, 512, S, false>, k_rows_split<R, L, 512, S, true>);

@@ -86,3 +86,26 @@ def test_paper_50_cubed_interior_solution_and_misfit():
     assert abs(e - printed) <= 0.02 * printed, (e, printed)
     assert abs(e - O.l2_misfit(p, ref.y, inst.ybar)) <= 1e-3 * printed
     prob.close()
+
+
+@pytest.mark.parametrize("n", [8, 12])
+def test_zero_initial_guess_matches_oracle_pcg_counts(n):
+    """inner_x0 = 1 (each sub-solve's PCG starts from zero, MATLAB pcg's default):
+    the GPU's FP64 PCG-ADMM takes the oracle's PCG iteration counts (within one per
+    sub-solve, rounding decides the last iteration) and lands on its iterates."""
+    need_gpu()
+    F = lib()
+    inst = paper_instance(n)
+    K = 6
+    ref = O.admm_pcg(inst, O.AdmmOptions(delta=0.4, rho=1.618), iters=K, inner_tol=1e-9, x0_zero=True)
+    prob = F.Problem(inst.params)
+    counts = []
+    for k in range(1, K + 1):
+        fo = F.AdmmOptions(delta=0.4, rho=1.618, max_admm=k, fixed_iters=True, inner_tol_mode=1, inner_tol=1e-9,
+                           inner_x0=1)
+        r = prob.admm_solve(fo, dev(inst.ybar), ya=inst.ya, yb=inst.yb, ua=inst.ua, ub=inst.ub, allow_noconv=True)
+        counts.append(r["stats"]["pcg_iters"])
+    per = np.diff([0] + counts)
+    assert np.all(np.abs(per - np.array(ref.pcg_iters)) <= 1), (per, ref.pcg_iters)
+    assert relerr(host(r["y"]), ref.y) < 1e-7
+    prob.close()

@@ -13,6 +13,7 @@ import pytest
 import torch
 
 import fde_inputs as fi
+import oracle as O
 from gpu_util import dev, host, lib, need_gpu, params, relerr
 
 pytestmark = pytest.mark.gpu
@@ -41,6 +42,23 @@ def test_noalloc_matches_fde_matvec_on_two_calls(dims, alpha):
             torch.cuda.synchronize()
             assert relerr(host(y), ref) < 1e-12, (call, op, relerr(host(y), ref))
     prob.close()
+
+
+@pytest.mark.parametrize("dims,alpha", [((8, 6, 20), 0.6), ((5, 19, 3), 1.0)])
+def test_noalloc_matches_the_oracle(dims, alpha):
+    """Independently of fde_matvec (which shares the transform kernels): B x and
+    B^T x against the FP64 oracle's per-axis dense products, including a time
+    axis of 20 steps with alpha_t = 0.6 (the embedded time transform of length 32)."""
+    need_gpu()
+    F = lib()
+    nx, ny, nt = dims
+    p = params(nx, ny, nt, alpha_t=alpha)
+    x = fi.random_field(7, (nt, nx, ny))
+    for op, tr in ((F.FDE_OP_B, False), (F.FDE_OP_BT, True)):
+        y = torch.full((p.N,), float("nan"), dtype=torch.float64, device="cuda")
+        assert _noalloc(F, p, op, dev(x), y) == F.FDE_OK
+        torch.cuda.synchronize()
+        assert relerr(host(y), O.apply_B(p, x, transpose=tr)) < 1e-12, (dims, op)
 
 
 def test_noalloc_rejects_sizes_beyond_its_array():
