@@ -3,8 +3,9 @@
 Parity: a batch of small uneven instances against the oracle's exact-sub-solve
 ADMM after K iterations, at the MIXED tolerance 1e-8. The 64-instance workload
 (grids 64^2..512^2, 16..64 steps) is checked for the invariants that hold at
-any size: every sub-problem met its relative-residual target, every result is
-finite, and a replayed graph reproduces the first launch bit for bit."""
+any size (every sub-problem met its relative-residual target, every result is
+finite, a replayed graph reproduces the first launch bit for bit) and, on its
+four smallest instances, against the oracle at 1e-8."""
 import numpy as np
 import pytest
 import torch
@@ -86,5 +87,17 @@ def test_batch_workload_64_uneven_instances():
     ys2, _, _ = b.admm_solve(fo, ybars, ua=ua, ub=ub)
     for a, y in zip(first, ys2):
         assert np.array_equal(a, host(y))
+    # the four smallest instances of the 64 against the oracle's PCG-ADMM after the same
+    # iterations, with every sub-problem solved tightly on both sides (1e-12 / 1e-13)
+    K = 2
+    tight = F.AdmmOptions(delta=1.0, rho=1.618, max_admm=K, inner_tol=1e-12, precision=F.FDE_MIXED_DFV,
+                          inner_tol_mixed=1e-5, max_refine=6, max_pcg=60)
+    ys, us, stats = b.admm_solve(tight, ybars, ua=ua, ub=ub)
+    smallest = sorted(range(len(insts)), key=lambda i: (insts[i].params.N, i))[:4]
+    for i in smallest:
+        assert stats[i]["max_sub_relres"] <= 1e-12, stats[i]
+        ref = O.admm_pcg(insts[i], O.AdmmOptions(delta=1.0, rho=1.618), iters=K, inner_tol=1e-13, max_pcg=2000)
+        assert relerr(host(ys[i]), ref.y) < 1e-8, (i, relerr(host(ys[i]), ref.y))
+        assert relerr(host(us[i]), ref.u) < 1e-8, (i, relerr(host(us[i]), ref.u))
     b.close()
     torch.cuda.empty_cache()
