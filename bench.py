@@ -769,8 +769,8 @@ def run_kernels(args):
     long_rows = prob.shape[2] > 2048
     for kind, x, y, kw, rows_list, axis_list in (
             ("f32", x32, y32, {}, (256, 128, 512), (512, 256)),
-            ("df", x64, y64, {"dfloat": True}, (256, -512, -256), (256, -512)),
-            ("f64", x64, y64, {"fp64": True}, (256, -512, -256), (256, -512))):
+            ("df", x64, y64, {"dfloat": True}, (256, -512, -256, 128), (256, -512, 128)),
+            ("f64", x64, y64, {"fp64": True}, (256, -512, -256, 128), (256, -512, 128))):
         fk = {"dfloat": True} if kind == "df" else {}
         for rows in rows_list:
             if long_rows and rows in (128, -256):

@@ -207,7 +207,8 @@ int fde_autotune(fde_problem* prob, void* stream);
  * float passes), FDE_MIXED_DF (the double-float passes) or FDE_FP64 (the double
  * passes): threads per CTA of the kernel that holds both embedding halves of a
  * line pair in each thread (float x2: 128, 256 or 512, x1: 256 or 512; double-float
- * and double: 256), or, negated, of the double-float or double split-halves
+ * and double: 128 or 256; 128 applies to lines of up to 2048, longer ones keep 256),
+ * or, negated, of the double-float or double split-halves
  * kernel whose two thread groups hold one half each (x2: 256 or 512, x1: 512). */
 int fde_tiles(const fde_problem* prob, int precision, int* rows_threads, int* axis_threads);
 

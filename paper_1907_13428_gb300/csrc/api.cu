@@ -782,8 +782,10 @@ int fde_set_tiles(fde_problem* P, int precision, int rows_threads, int axis_thre
     rows_ok = rows_threads == 0 || rows_threads == 256 || rows_threads == 512 || (!long_rows && rows_threads == 128);
     axis_ok = axis_threads == 0 || axis_threads == 512 || axis_threads == 256;
   } else {
-    rows_ok = rows_threads == 0 || rows_threads == 256 || rows_threads == -512 || (!long_rows && rows_threads == -256);
-    axis_ok = axis_threads == 0 || axis_threads == 256 || axis_threads == -512;
+    rows_ok = rows_threads == 0 || rows_threads == 256 || rows_threads == -512 ||
+              (!long_rows && (rows_threads == -256 || rows_threads == 128));
+    // 128 threads: lines of up to 2048 (longer lines keep the 256-thread tile)
+    axis_ok = axis_threads == 0 || axis_threads == 256 || axis_threads == -512 || axis_threads == 128;
   }
   if (!rows_ok || !axis_ok) return FDE_EINVAL;
   int *rf, *af;

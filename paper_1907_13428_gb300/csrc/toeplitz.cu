@@ -397,6 +397,7 @@ cudaError_t autotune_tiles(fde_problem* P, const float* x, float* y, const doubl
       const int c = cand[i];
       // the 128-thread and 256-thread split x2 tiles need a line of at most 2048
       if (short_only_mask && (c == 128 || c == -256) && P->ax[axis].L > 2048) continue;
+      if (c == 128 && P->ax[axis].L > 2048) continue;
       *field = c;
       const cudaError_t r = time_it(axis, kind, &ms);
       if (r != cudaSuccess) return r;
@@ -411,14 +412,14 @@ cudaError_t autotune_tiles(fde_problem* P, const float* x, float* y, const doubl
   };
   const int rows32[3] = {256, 128, 512};
   const int axis32[2] = {512, 256};
-  const int rows64[3] = {256, -512, -256};
-  const int axis64[2] = {256, -512};
+  const int rows64[4] = {256, -512, -256, 128};
+  const int axis64[3] = {256, -512, 128};
   if (e == cudaSuccess) e = tune(&P->rows_nt32, rows32, 3, 2, 0, true);
   if (e == cudaSuccess) e = tune(&P->axis_nt32, axis32, 2, 1, 0, false);
-  if (e == cudaSuccess) e = tune(&P->rows_ntdd, rows64, 3, 2, 1, true);
-  if (e == cudaSuccess) e = tune(&P->axis_ntdd, axis64, 2, 1, 1, false);
-  if (e == cudaSuccess) e = tune(&P->rows_nt64, rows64, 3, 2, 2, true);
-  if (e == cudaSuccess) e = tune(&P->axis_nt64, axis64, 2, 1, 2, false);
+  if (e == cudaSuccess) e = tune(&P->rows_ntdd, rows64, 4, 2, 1, true);
+  if (e == cudaSuccess) e = tune(&P->axis_ntdd, axis64, 3, 1, 1, false);
+  if (e == cudaSuccess) e = tune(&P->rows_nt64, rows64, 4, 2, 2, true);
+  if (e == cudaSuccess) e = tune(&P->axis_nt64, axis64, 3, 1, 2, false);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   return e;

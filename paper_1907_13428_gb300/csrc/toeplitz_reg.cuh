@@ -397,8 +397,8 @@ static cudaError_t launch_rows_split_LN(fde_problem* P, const S* x, int conj_sym
 }
 
 // The tile chosen by fde_autotune: float 128, 256 or 512 threads; double and
-// double-float 256 threads, or the split-halves variant with 256 or 512 threads
-// (stored negated).
+// double-float 128 (lines up to 2048) or 256 threads, or the split-halves variant
+// with 256 or 512 threads (stored negated).
 template <typename R, int L, typename S>
 cudaError_t launch_rows_reg_L(fde_problem* P, const S* x, int conj_sym, const cplx<R>* sym,
                                      const AxisTables<R>& T, const AxisEpi<S>& E, cudaStream_t st) {
@@ -412,6 +412,10 @@ cudaError_t launch_rows_reg_L(fde_problem* P, const S* x, int conj_sym, const cp
     const int choice = std::is_same<R, dd>::value ? P->rows_ntdd : P->rows_nt64;
     if constexpr (2 * (L / 16) <= 256) {
       if (choice == -256) return launch_rows_split_LN<R, L, 256, S>(P, x, conj_sym, sym, T, E, st);
+    }
+    if constexpr (L / 16 <= 128) {
+      // two CTAs of 128 threads per SM: one CTA's exchanges overlap the other's arithmetic
+      if (choice == 128) return launch_rows_reg_LN<R, L, 128, S>(P, x, conj_sym, sym, T, E, st);
     }
     if (choice == -512) return launch_rows_split_LN<R, L, 512, S>(P, x, conj_sym, sym, T, E, st);
   }
@@ -475,6 +479,11 @@ cudaError_t launch_axis_reg_L(const S* x, int n, long long axis_stride, long lon
     if (nt_choice == -512)
       return launch_axis_split_LN<R, L, 512, S>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym,
                                                 E, st);
+    if constexpr (L / 16 <= 128) {
+      if (nt_choice == 128)
+        return launch_axis_reg_LN<R, L, 128, S>(x, n, axis_stride, n_inner, outer_stride, n_outer, sym, T, conj_sym,
+                                                E, st);
+    }
   }
   if constexpr (sizeof(R) == 4) {
     if (nt_choice == 256)
@@ -539,6 +548,10 @@ cudaError_t reg_attrs_L() {
     smem_attr(e, k_rows_split<R, L, 512, S, false>, k_rows_split<R, L, 512, S, true>);
     smem_attr(e, k_axis_split<R, L, 512, S, false>, k_axis_split<R, L, 512, S, true>);
     if constexpr (L <= 2048) smem_attr(e, k_rows_split<R, L, 256, S, false>, k_rows_split<R, L, 256, S, true>);
+    if constexpr (L / 16 <= 128) {
+      smem_attr(e, k_rows_reg<R, L, 128, S, false>, k_rows_reg<R, L, 128, S, true>);
+      smem_attr(e, k_axis_reg<R, L, 128, S, false>, k_axis_reg<R, L, 128, S, true>);
+    }
   }
   return e;
 }
