@@ -230,7 +230,7 @@ def test_batch_mixed_dfv_matches_oracle():
     b.close()
 
 
-@pytest.mark.parametrize("tiles", [(256, 256), (-512, -512), (-256, -512)])
+@pytest.mark.parametrize("tiles", [(256, 256), (-512, -512), (-256, -512), (128, 128)])
 @pytest.mark.parametrize("dims", [(17, 33, 6), (64, 64, 4), (100, 50, 3), (31, 200, 2), (2, 1100, 2)])
 def test_every_dfloat_tile_matches_oracle(dims, tiles):
     """Both double-float tile variants (both halves per thread, split halves) of
@@ -241,7 +241,7 @@ def test_every_dfloat_tile_matches_oracle(dims, tiles):
     p = params(nx, ny, nt)
     prob = F.Problem(p)
     rows, axis = tiles
-    if ny > 2048 and rows == -256:
+    if ny > 2048 and rows in (-256, 128):
         rows = 0
     prob.set_tiles(rows, axis, dfloat=True)
     assert prob.tiles(dfloat=True)[1] == axis

@@ -177,11 +177,11 @@ def test_autotuned_tiles_keep_parity(dims):
     p = params(nx, ny, nt)
     prob = F.Problem(p)
     rows, axis = prob.autotune()
-    assert rows in (128, 256) and axis in (256, 512)
+    assert rows in (128, 256, 512) and axis in (256, 512)
     rd, ad = prob.tiles(dfloat=True)
-    assert rd in (256, -256, -512) and ad in (256, -512)
+    assert rd in (128, 256, -256, -512) and ad in (128, 256, -512)
     r64, a64 = prob.tiles(fp64=True)
-    assert r64 in (256, -256, -512) and a64 in (256, -512)
+    assert r64 in (128, 256, -256, -512) and a64 in (128, 256, -512)
     assert relerr(host(prob.matvec(dev(fi.random_field(3, (nt, nx, ny))), dfloat=True)),
                   O.apply_B(p, fi.random_field(3, (nt, nx, ny)))) < 1e-11
     x = fi.random_field(31, (nt, nx, ny))
@@ -191,7 +191,7 @@ def test_autotuned_tiles_keep_parity(dims):
     prob.close()
 
 
-@pytest.mark.parametrize("tiles", [(128, 256), (256, 512), (128, 512), (256, 256)])
+@pytest.mark.parametrize("tiles", [(128, 256), (256, 512), (128, 512), (256, 256), (512, 512)])
 @pytest.mark.parametrize("dims", [(7, 5, 3), (33, 17, 6), (64, 64, 4), (100, 50, 3), (17, 300, 2), (2, 1100, 2)])
 def test_every_float_tile_matches_oracle(dims, tiles):
     """Each float tile of the x2 and x1 passes: B, B^T and S against the oracle,
@@ -227,7 +227,7 @@ def test_set_tiles_rejects_unknown_values():
         with pytest.raises(F.FdeError) as e:
             prob.set_tiles(*bad)
         assert e.value.status == F.FDE_EINVAL
-    for bad in ((128, 0), (0, 512), (-128, 0), (0, -256)):
+    for bad in ((64, 0), (512, 0), (0, 512), (-128, 0), (0, -256)):
         for kw in (dict(dfloat=True), dict(fp64=True)):
             with pytest.raises(F.FdeError) as e:
                 prob.set_tiles(*bad, **kw)
@@ -235,7 +235,7 @@ def test_set_tiles_rejects_unknown_values():
     prob.close()
 
 
-@pytest.mark.parametrize("tiles", [(256, 256), (-512, -512), (-256, -512), (256, -512)])
+@pytest.mark.parametrize("tiles", [(256, 256), (-512, -512), (-256, -512), (256, -512), (128, 128)])
 @pytest.mark.parametrize("dims", [(7, 5, 3), (17, 33, 6), (64, 64, 4), (100, 50, 3), (31, 200, 2), (2, 1100, 2)])
 def test_every_fp64_tile_matches_oracle(dims, tiles):
     """Each double tile of the x2 and x1 passes (both halves per thread, split
@@ -247,7 +247,7 @@ def test_every_fp64_tile_matches_oracle(dims, tiles):
     p = params(nx, ny, nt)
     prob = F.Problem(p)
     rows, axis = tiles
-    if ny > 2048 and rows == -256:
+    if ny > 2048 and rows in (-256, 128):
         rows = 0
     prob.set_tiles(rows, axis, fp64=True)
     assert prob.tiles(fp64=True) == (rows or 256, axis)
@@ -282,7 +282,7 @@ def test_largest_axis_length(dims, alpha):
         ref = O.apply_B(p, x, transpose=tr)
         assert relerr(host(prob.matvec(xd, op)), ref) < 1e-12
         assert relerr(host(prob.matvec(xd.float(), op)), ref) < 5e-5
-        for rows, axis in ((256, 256), (-512, -512)):
+        for rows, axis in ((256, 256), (-512, -512), (256, 128)):
             prob.set_tiles(rows, axis, dfloat=True)
             assert relerr(host(prob.matvec(xd, op, dfloat=True)), ref) < 1e-11, (rows, axis)
             prob.set_tiles(rows, axis, fp64=True)
