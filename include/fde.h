@@ -49,7 +49,8 @@ enum fde_status {
   FDE_ENOCONV = -4,      /* iteration cap reached; outputs hold the last iterate           */
   FDE_EBREAKDOWN = -5,   /* PCG breakdown (p^T S p <= 0)                                   */
   FDE_ENONFINITE = -6,   /* NaN or Inf met in a reduction                                  */
-  FDE_EUNSUPPORTED = -8  /* size or mode the library does not handle                      */
+  FDE_EUNSUPPORTED = -8, /* size or mode the library does not handle                      */
+  FDE_ETIMEOUT = -9      /* a bounded device-side wait of the persistent batch solve ran out */
 };
 
 /* Arithmetic of an operator application or of a solve. */
@@ -350,11 +351,61 @@ long long fde_batch_instance_size(const fde_batch* batch, int i);
  * (device, N_i doubles); stats (HOST array of `count`, may be NULL;
  * max_sub_relres is the largest final relative residual over the
  * sub-problems). Synchronises `stream`. Errors: FDE_EINVAL (opts->precision
- * not FDE_MIXED or FDE_MIXED_DF, NULL pointers, NaN bounds), FDE_ENONFINITE,
- * FDE_ECUDA. */
+ * not FDE_MIXED, FDE_MIXED_DF or FDE_MIXED_DFV, NULL pointers, NaN bounds),
+ * FDE_EUNSUPPORTED (opts->inner_solver, warm_start or inner_x0 set),
+ * FDE_ENONFINITE, FDE_ECUDA. */
 int fde_batch_admm_solve(fde_batch* batch, const fde_admm_opts* opts, const double* const* ybar,
                          const double* ya, const double* yb, const double* ua, const double* ub,
                          double* const* y, double* const* u, fde_admm_stats* stats, void* stream);
+
+/* Configuration of the persistent batch solve. Zero fields take the defaults. */
+typedef struct fde_persist_cfg {
+  int group_ctas;    /* CTAs that solve one instance together (an instance group);
+                        0: the resident CTAs divided into 16 groups (one group for a
+                        batch of one); clamped to the resident CTAs                       */
+  double timeout_s;  /* limit of every device-side wait (0: 1 s)                          */
+  int replay;        /* 0: the persistent kernel; 1: the same recorded launches issued
+                        one by one on `stream` (the reference executor of the tests)      */
+  int stall_group;   /* test hook, 0: off. k > 0: the first CTA of instance group k - 1
+                        never arrives at its first group barrier, so that every wait of
+                        that group runs out                                               */
+} fde_persist_cfg;
+
+/* What a persistent solve ran (HOST struct, filled on return). */
+typedef struct fde_persist_info {
+  long long commands;     /* recorded launches over all instances                        */
+  int groups;             /* instance groups                                             */
+  int group_ctas;         /* CTAs per group                                              */
+  int ctas_per_sm;        /* resident CTAs per SM of the persistent kernel               */
+  int smem_bytes;         /* dynamic shared memory per CTA                               */
+  int timeout_group;      /* on FDE_ETIMEOUT: the group whose wait ran out, else -1      */
+  long long timeout_command; /* ... and the index of the command it had finished         */
+} fde_persist_info;
+
+/* The batch solve of fde_batch_admm_solve (same arguments, options and fixed
+ * iteration budgets; opts->precision must be FDE_MIXED: the executor has no
+ * double-float transforms) run by ONE persistent cooperative kernel.
+ * The launches that fde_batch_admm_solve would capture into its graph are
+ * recorded instead (every transform in its generic shared-memory form, every
+ * launch with 256 threads); the kernel keeps ctas_per_sm x SMs CTAs resident,
+ * split into instance groups of cfg->group_ctas CTAs. A group takes the next
+ * instance from a device-side queue (largest instances first), runs the
+ * bodies of that instance's recorded launches one after another (each launch's
+ * blocks spread over the group's CTAs) with a group barrier after each, and
+ * takes the next instance until the queue is empty. Every barrier wait is
+ * bounded by cfg->timeout_s: when one runs out the kernel records the group
+ * and command, every CTA returns within about one more limit, and the call
+ * returns FDE_ETIMEOUT with the context usable. cfg may be NULL (defaults);
+ * info may be NULL. Every axis length (nx, ny, nt) must be a power of two
+ * (the executor's transforms are the radix-4/2 ones) and at most 2048.
+ * Synchronises `stream`. Errors: FDE_EINVAL (as fde_batch_admm_solve;
+ * precision not FDE_MIXED; a negative cfg field), FDE_EUNSUPPORTED (an axis
+ * that is not a power of two or above 2048, a command the executor cannot
+ * replay), FDE_ETIMEOUT, FDE_ENONFINITE, FDE_ENOMEM, FDE_ECUDA. */
+int fde_batch_admm_solve_persistent(fde_batch* batch, const fde_admm_opts* opts, const double* const* ybar,
+                                    const double* ya, const double* yb, const double* ua, const double* ub,
+                                    double* const* y, double* const* u, const fde_persist_cfg* cfg,
+                                    fde_admm_stats* stats, fde_persist_info* info, void* stream);
 
 /* Arithmetic peak of this GPU measured with independent fused multiply-add
  * chains (precision FDE_FP64 or FDE_FP32), in TFLOP/s, best of three runs of

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfde.so")
 
 FDE_OK, FDE_EINVAL, FDE_ENOMEM, FDE_ECUDA, FDE_ENOCONV = 0, -1, -2, -3, -4
-FDE_EBREAKDOWN, FDE_ENONFINITE, FDE_EUNSUPPORTED = -5, -6, -8
+FDE_EBREAKDOWN, FDE_ENONFINITE, FDE_EUNSUPPORTED, FDE_ETIMEOUT = -5, -6, -8, -9
 FDE_FP64, FDE_FP32, FDE_MIXED, FDE_MIXED_DF, FDE_MIXED_DFV = 0, 1, 2, 3, 4
 FDE_OP_B, FDE_OP_BT, FDE_OP_S = 0, 1, 2
 
@@ -46,6 +46,20 @@ class fde_admm_stats(ctypes.Structure):
                 ("res_u", ctypes.c_double), ("objective", ctypes.c_double), ("max_sub_relres", ctypes.c_double),
                 ("recursive_steers", ctypes.c_int), ("copy_in_ms", ctypes.c_double),
                 ("copy_out_ms", ctypes.c_double), ("float_steers", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fde_persist_cfg(ctypes.Structure):
+    _fields_ = [("group_ctas", ctypes.c_int), ("timeout_s", ctypes.c_double), ("replay", ctypes.c_int),
+                ("stall_group", ctypes.c_int)]
+
+
+class fde_persist_info(ctypes.Structure):
+    _fields_ = [("commands", ctypes.c_longlong), ("groups", ctypes.c_int), ("group_ctas", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int), ("smem_bytes", ctypes.c_int), ("timeout_group", ctypes.c_int),
+                ("timeout_command", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -81,6 +95,10 @@ _SIGS = {
     "fde_batch_instance_size": (ctypes.c_longlong, [_P, ctypes.c_int]),
     "fde_batch_admm_solve": (ctypes.c_int, [_P, ctypes.POINTER(fde_admm_opts), _P, _P, _P, _P, _P, _P, _P,
                                             ctypes.POINTER(fde_admm_stats), _P]),
+    "fde_batch_admm_solve_persistent": (ctypes.c_int, [_P, ctypes.POINTER(fde_admm_opts), _P, _P, _P, _P, _P, _P,
+                                                       _P, ctypes.POINTER(fde_persist_cfg),
+                                                       ctypes.POINTER(fde_admm_stats),
+                                                       ctypes.POINTER(fde_persist_info), _P]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -379,7 +397,8 @@ class Problem:
 
 class Batch:
     """Owner of an fde_batch: independent instances solved together in one
-    CUDA-graph launch (fde_batch_admm_solve)."""
+    CUDA-graph launch (fde_batch_admm_solve) or in one persistent cooperative
+    kernel (fde_batch_admm_solve_persistent)."""
 
     def __init__(self, params_list):
         self.params = list(params_list)
@@ -427,6 +446,40 @@ class Batch:
                                        u_ptrs, st, _stream())
         _check(s, "fde_batch_admm_solve")
         return ys, us, [x.as_dict() for x in st]
+
+    def admm_solve_persistent(self, opts: AdmmOptions, ybars, ya=None, yb=None, ua=None, ub=None, out=None,
+                              group_ctas: int = 0, timeout_s: float = 0.0, replay: bool = False,
+                              stall_group: int = 0, check: bool = True):
+        """The same batch solve run by one persistent cooperative kernel
+        (fde_batch_admm_solve_persistent; FDE_MIXED only). replay=True issues the
+        recorded launches one by one instead (reference executor). Returns
+        (ys, us, stats list, info dict, status); with check=True a failing status
+        raises FdeError."""
+        n = len(self.sizes)
+        if out is None:
+            if self._out is None:
+                self._out = ([torch.empty(N, dtype=torch.float64, device=ybars[0].device) for N in self.sizes],
+                             [torch.empty(N, dtype=torch.float64, device=ybars[0].device) for N in self.sizes])
+            out = self._out
+        ys, us = out
+        P = ctypes.c_void_p
+        yb_ptrs = (P * n)(*[_ptr(t, torch.float64, N).value for t, N in zip(ybars, self.sizes)])
+        y_ptrs = (P * n)(*[t.data_ptr() for t in ys])
+        u_ptrs = (P * n)(*[t.data_ptr() for t in us])
+
+        def arr(v):
+            return None if v is None else (ctypes.c_double * n)(*[float(a) for a in v])
+
+        st = (fde_admm_stats * n)()
+        info = fde_persist_info()
+        cfg = fde_persist_cfg(int(group_ctas), float(timeout_s), int(bool(replay)), int(stall_group))
+        o = opts.c()
+        s = lib().fde_batch_admm_solve_persistent(self._h, ctypes.byref(o), yb_ptrs, arr(ya), arr(yb), arr(ua),
+                                                  arr(ub), y_ptrs, u_ptrs, ctypes.byref(cfg), st,
+                                                  ctypes.byref(info), _stream())
+        if check:
+            _check(s, "fde_batch_admm_solve_persistent")
+        return ys, us, [x.as_dict() for x in st], info.as_dict(), s
 
 
 class FdeAdmmFn(torch.autograd.Function):

@@ -3,12 +3,16 @@
 // the ADMM driver (Algorithm 1 with the sub-problem merged with the p update,
 // Section 3.1; psi scaling and stopping rules of Section 6.1), and the
 // gradient of the optimal value.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <numeric>
+#include <vector>
 
 #include "internal.h"
+#include "persist.h"
 #include "saddle.h"
 #include "vec.h"
 
@@ -641,6 +645,7 @@ const char* fde_strerror(int s) {
     case FDE_EBREAKDOWN: return "PCG breakdown (non-positive curvature)";
     case FDE_ENONFINITE: return "non-finite value in a reduction";
     case FDE_EUNSUPPORTED: return "unsupported size or mode";
+    case FDE_ETIMEOUT: return "a bounded device-side wait ran out";
     default: return "unknown status";
   }
 }
@@ -1185,7 +1190,8 @@ int enqueue_admm_fixed(fde_problem* P, const fde_admm_opts* o, const double* yba
   AdmmArgs A = make_admm_args(P, o, dg, ybar, nullptr, nullptr, nullptr, nullptr, nullptr, ya_s, yb_s, ua_s, ub_s);
   double* Y = P->v64[V_Y];
   double* U = P->v64[V_U];
-  CK(cudaMemsetAsync(P->dscal, 0, sizeof(double) * S_COUNT, st));
+  // kernels only (no memset or memcpy nodes), so that the launches can also be recorded
+  CK(fill<double>(P->dscal, 0.0, S_COUNT, st));
   for (int i : {V_Y, V_U, V_ZY, V_ZU, V_P, V_WY, V_WU, V_BY}) CK(fill<double>(P->v64[i], 0.0, N, st));
   const long long last = (long long)(P->nt - 1) * P->nx * P->ny;
   const SliceDiag one{{1.0, 1.0}};
@@ -1228,8 +1234,8 @@ int enqueue_admm_fixed(fde_problem* P, const fde_admm_opts* o, const double* yba
     CK(scalar_max(P, S_MAXREL, S_RELRES, st));
     CK(admm_post(P, A, Y, P->v64[V_BY], P->v64[V_BU], P->v64[V_R0], U, st));
   }
-  CK(cudaMemcpyAsync(y, Y, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(u, U, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  CK(copy<double>(y, Y, N, st));
+  CK(copy<double>(u, U, N, st));
   return FDE_OK;
 }
 
@@ -1262,6 +1268,20 @@ struct fde_batch {
   double** u = nullptr;
   double* bounds = nullptr;  // 4 per instance: ya, yb, ua, ub
   long long kernels = 0;     // kernel nodes of the captured graph
+  // persistent solve: the recorded launches and the arguments they were recorded with
+  bool rec_valid = false;
+  fde_admm_opts rec_opts{};
+  std::vector<const double*> rec_ybar;
+  std::vector<double*> rec_y, rec_u;
+  std::vector<double> rec_bounds;
+  std::vector<unsigned char> rec_cmds;  // host copy (stream replay)
+  std::vector<long long> rec_off;
+  size_t rec_smem = 0;
+  unsigned char* d_cmds = nullptr;  // device copy of the commands
+  long long* d_off = nullptr;
+  int* d_order = nullptr;
+  void* d_state = nullptr;  // barrier counters, queue, slots, status
+  int state_groups = 0;
 };
 
 extern "C" {
@@ -1276,6 +1296,10 @@ void fde_batch_destroy(fde_batch* b) {
   }
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->capture) cudaStreamDestroy(b->capture);
+  if (b->d_cmds) cudaFree(b->d_cmds);
+  if (b->d_off) cudaFree(b->d_off);
+  if (b->d_order) cudaFree(b->d_order);
+  if (b->d_state) cudaFree(b->d_state);
   delete[] b->probs;
   delete[] b->streams;
   delete[] b->joins;
@@ -1406,6 +1430,170 @@ int fde_batch_admm_solve(fde_batch* b, const fde_admm_opts* o, const double* con
   CK(cudaGraphLaunch(b->exec, st));
   note_launches((int)b->kernels);
   CK(cudaStreamSynchronize(st));
+  int status = FDE_OK;
+  for (int i = 0; i < n; ++i) {
+    fde_problem* P = b->probs[i];
+    CK(cudaMemcpy(P->hscal, P->dscal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost));
+    if (stats) stats_from_scalars(P->hscal, o->max_admm, &stats[i]);
+    const int flag = (int)P->hscal[S_FLAG];
+    if (flag < 0 && status == FDE_OK) status = flag;
+  }
+  return status;
+}
+
+
+int fde_batch_admm_solve_persistent(fde_batch* b, const fde_admm_opts* o, const double* const* ybar,
+                                    const double* ya, const double* yb, const double* ua, const double* ub,
+                                    double* const* y, double* const* u, const fde_persist_cfg* cfg,
+                                    fde_admm_stats* stats, fde_persist_info* info, void* stream) {
+  if (info) {
+    *info = fde_persist_info{};
+    info->timeout_group = -1;
+    info->timeout_command = -1;
+  }
+  if (!b || !valid_opts(o) || !ybar || !y || !u) return FDE_EINVAL;
+  if (o->precision != FDE_MIXED || o->max_admm < 1 || o->max_pcg < 1) return FDE_EINVAL;
+  if (cfg && (cfg->group_ctas < 0 || !(cfg->timeout_s >= 0.0) || cfg->stall_group < 0)) return FDE_EINVAL;
+  const int n = b->count;
+  for (int i = 0; i < n; ++i) {
+    if (!valid_opts_for(b->probs[i], o)) return FDE_EINVAL;
+    if (!ybar[i] || !y[i] || !u[i]) return FDE_EINVAL;
+  }
+  if (o->inner_solver != 0 || o->warm_start || o->inner_x0) return FDE_EUNSUPPORTED;
+  auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+  for (int i = 0; i < n; ++i) {
+    // the generic passes of a 256-thread block hold at least one line pair of 2L;
+    // the executor's transforms are the power-of-two ones (the preconditioner
+    // transforms the exact axis lengths)
+    const fde_problem* P = b->probs[i];
+    if (P->ax[1].L > 2048 || P->ax[2].L > 2048 || (!P->euler && P->ax[0].L > 2048)) return FDE_EUNSUPPORTED;
+    if (!pow2(P->nx) || !pow2(P->ny) || !pow2(P->nt)) return FDE_EUNSUPPORTED;
+  }
+  std::vector<double> bd(4 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    const double v[4] = {ya ? ya[i] : -INFINITY, yb ? yb[i] : INFINITY, ua ? ua[i] : -INFINITY, ub ? ub[i] : INFINITY};
+    for (int k = 0; k < 4; ++k) {
+      if (std::isnan(v[k])) return FDE_EINVAL;
+      bd[4 * i + k] = v[k];
+    }
+  }
+  bool same = b->rec_valid && std::memcmp(&b->rec_opts, o, sizeof(*o)) == 0 && b->rec_bounds == bd;
+  for (int i = 0; i < n && same; ++i) same = b->rec_ybar[i] == ybar[i] && b->rec_y[i] == y[i] && b->rec_u[i] == u[i];
+  if (!same) {
+    // record every instance's launches; a stream capture around the recording
+    // catches any launch that did not go through the recorder
+    b->rec_valid = false;
+    Recorder rec;
+    std::vector<long long> off(n + 1, 0);
+    CK(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
+    active_recorder() = &rec;
+    int status = FDE_OK;
+    for (int i = 0; i < n && status == FDE_OK; ++i) {
+      off[i] = rec.count();
+      status = enqueue_admm_fixed(b->probs[i], o, ybar[i], bd[4 * i], bd[4 * i + 1], bd[4 * i + 2], bd[4 * i + 3],
+                                  y[i], u[i], b->capture);
+    }
+    active_recorder() = nullptr;
+    off[n] = rec.count();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->capture, &graph);
+    size_t stray = 0;
+    if (graph) {
+      cudaGraphGetNodes(graph, nullptr, &stray);
+      cudaGraphDestroy(graph);
+    }
+    if (status != FDE_OK) return status;
+    CK(ec);
+    if (rec.error) return FDE_EUNSUPPORTED;
+    if (stray != 0) {
+      std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%zu launches escaped the recorder", stray);
+      return FDE_ECUDA;
+    }
+    // queue order: largest instances first
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->probs[a]->N > b->probs[c]->N; });
+    if (b->d_cmds) cudaFree(b->d_cmds);
+    if (b->d_off) cudaFree(b->d_off);
+    if (b->d_order) cudaFree(b->d_order);
+    b->d_cmds = nullptr;
+    b->d_off = nullptr;
+    b->d_order = nullptr;
+    if (cudaMalloc(&b->d_cmds, rec.cmds.size()) != cudaSuccess ||
+        cudaMalloc(&b->d_off, sizeof(long long) * (n + 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_order, sizeof(int) * n) != cudaSuccess)
+      return FDE_ENOMEM;
+    CK(cudaMemcpy(b->d_cmds, rec.cmds.data(), rec.cmds.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->d_off, off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    b->rec_cmds.swap(rec.cmds);
+    b->rec_off.swap(off);
+    b->rec_smem = rec.max_smem;
+    b->rec_opts = *o;
+    b->rec_bounds = bd;
+    b->rec_ybar.assign(ybar, ybar + n);
+    b->rec_y.assign(y, y + n);
+    b->rec_u.assign(u, u + n);
+    b->rec_valid = true;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long ncmd = b->rec_off[n];
+  int cps = 0, dev = 0, sms = 0;
+  CK(fde::persist_prepare(b->rec_smem, &cps));
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (cps < 1) return FDE_EUNSUPPORTED;
+  const int total = cps * sms;
+  int gc = (cfg && cfg->group_ctas > 0) ? cfg->group_ctas : total / std::min(16, n);
+  gc = std::max(1, std::min(gc, total));
+  const int groups = total / gc;
+  if (info) {
+    info->commands = ncmd;
+    info->groups = groups;
+    info->group_ctas = gc;
+    info->ctas_per_sm = cps;
+    info->smem_bytes = (int)b->rec_smem;
+  }
+  if (cfg && cfg->replay) {
+    CK(fde::persist_replay(b->rec_cmds.data(), ncmd, st));
+    CK(cudaStreamSynchronize(st));
+  } else {
+    // executor state: [groups] counters, queue, [groups] slots, then 4 status words
+    const size_t bytes = sizeof(long long) * 4 + sizeof(unsigned) * groups + sizeof(int) * (groups + 1);
+    if (b->state_groups < groups) {
+      if (b->d_state) cudaFree(b->d_state);
+      b->d_state = nullptr;
+      b->state_groups = 0;
+      if (cudaMalloc(&b->d_state, bytes) != cudaSuccess) return FDE_ENOMEM;
+      b->state_groups = groups;
+    }
+    CK(cudaMemsetAsync(b->d_state, 0, bytes, st));
+    fde::PersistLaunch pl{};
+    pl.status = reinterpret_cast<long long*>(b->d_state);
+    pl.bar = reinterpret_cast<unsigned*>(pl.status + 4);
+    pl.queue = reinterpret_cast<int*>(pl.bar + groups);
+    pl.slot = pl.queue + 1;
+    pl.cmds = b->d_cmds;
+    pl.off = b->d_off;
+    pl.order = b->d_order;
+    pl.count = n;
+    pl.groups = groups;
+    pl.group_ctas = gc;
+    const double lim = (cfg && cfg->timeout_s > 0.0) ? cfg->timeout_s : 1.0;
+    pl.timeout_ns = (unsigned long long)(lim * 1e9);
+    pl.stall_group = (cfg && cfg->stall_group > 0) ? cfg->stall_group - 1 : -1;
+    CK(fde::persist_run(pl, b->rec_smem, st));
+    CK(cudaStreamSynchronize(st));
+    long long hs[4];
+    CK(cudaMemcpy(hs, pl.status, sizeof(hs), cudaMemcpyDeviceToHost));
+    if (hs[0] != 0) {
+      if (info) {
+        info->timeout_group = (int)hs[1];
+        info->timeout_command = hs[2];
+      }
+      return (int)hs[0];
+    }
+  }
   int status = FDE_OK;
   for (int i = 0; i < n; ++i) {
     fde_problem* P = b->probs[i];

@@ -151,4 +151,26 @@ __device__ __forceinline__ void smem_fft(cplx<R>* buf, int nlines, int lstride, 
   }
 }
 
+// smem_fft for power-of-two lengths (plans of radix-4 passes and at most one
+// radix-2 pass): the same passes with only those two radices compiled in.
+template <typename R, int EPT>
+__device__ __forceinline__ void smem_fft_pow2(cplx<R>* buf, int nlines, int lstride, const FftPlan& pl,
+                                              const cplx<R>* __restrict__ tw, bool inv) {
+  int Ns = 1;
+  for (int s = 0; s < pl.nstages; ++s) {
+    if (pl.radix[s] == 4) stockham_pass<R, 4, EPT>(buf, nlines, lstride, pl.L, Ns, tw, inv);
+    else stockham_pass<R, 2, EPT>(buf, nlines, lstride, pl.L, Ns, tw, inv);
+    Ns *= pl.radix[s];
+  }
+}
+
+// The transform of the generic passes: inside the persistent executor (PS),
+// whose problems have power-of-two axes, the power-of-two form.
+template <bool PS, typename R, int EPT>
+__device__ __forceinline__ void lines_fft(cplx<R>* buf, int nlines, int lstride, const FftPlan& pl,
+                                          const cplx<R>* __restrict__ tw, bool inv) {
+  if constexpr (PS) smem_fft_pow2<R, EPT>(buf, nlines, lstride, pl, tw, inv);
+  else smem_fft<R, EPT>(buf, nlines, lstride, pl, tw, inv);
+}
+
 }  // namespace fde

@@ -7,6 +7,7 @@
 
 #include "../../include/fde.h"
 #include "common.cuh"
+#include "op.cuh"
 
 namespace fde {
 
@@ -108,9 +109,10 @@ enum Scal {
   S_COUNT = 32
 };
 
-__device__ __forceinline__ bool gate_closed(const Gate& g) {
-  if (g.mode == 1) return g.dscal[S_RR] <= g.dscal[S_THR];
-  if (g.mode == 2) return g.dscal[S_CONV] != 0.0;
+// PS: the scalars may have been written earlier in the same (persistent) kernel.
+template <bool PS = false> __device__ __forceinline__ bool gate_closed(const Gate& g) {
+  if (g.mode == 1) return ldv<PS>(g.dscal + S_RR) <= ldv<PS>(g.dscal + S_THR);
+  if (g.mode == 2) return ldv<PS>(g.dscal + S_CONV) != 0.0;
   return false;
 }
 

@@ -16,145 +16,24 @@
 //   4. x1 columns: inverse DFT;
 //   5. x2 rows: the two Hermitian half spectra are recombined into one complex
 //      line, inverse DFT, real and imaginary parts are the two output rows.
-#include "internal.h"
+#include "ops_prec.cuh"
 
 namespace fde {
-
-constexpr int kPEPT = 16;
 
 template <typename R> static const AxisTables<R>& ptables(const Axis& A);
 template <> const AxisTables<double>& ptables<double>(const Axis& A) { return A.d; }
 template <> const AxisTables<float>& ptables<float>(const Axis& A) { return A.f; }
 
-// Step 1: rows of r -> half spectra.
-template <typename R>
-__global__ void __launch_bounds__(512) k_prec_rows_fwd(const R* __restrict__ r, cplx<R>* __restrict__ spec,
-                                                        long long nrows, int n, int H, int Hp,
-                                                        const cplx<R>* __restrict__ twn, FftPlan pl, int pairs, Gate gate) {
-  if (gate_closed(gate)) return;
-  using C = cplx<R>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  const long long row0 = (long long)blockIdx.x * pairs * 2;
-  for (int e = threadIdx.x; e < pairs * n; e += blockDim.x) {
-    const int p = e / n, j = e - p * n;
-    const long long ra = row0 + 2 * p, rb = ra + 1;
-    const R a = ra < nrows ? r[ra * n + j] : (R)0;
-    const R b = rb < nrows ? r[rb * n + j] : (R)0;
-    buf[p * n + j] = mk<C>(a, b);
-  }
-  __syncthreads();
-  smem_fft<R, kPEPT>(buf, pairs, n, pl, twn, false);
-  for (int e = threadIdx.x; e < pairs * H; e += blockDim.x) {
-    const int p = e / H, k = e - p * H;
-    const long long ra = row0 + 2 * p, rb = ra + 1;
-    const C zk = buf[p * n + k];
-    const C zm = cconj(buf[p * n + (k == 0 ? 0 : n - k)]);
-    // A = (Z_k + conj Z_{-k}) / 2,  B = (Z_k - conj Z_{-k}) / (2i)
-    const C A = mk<C>((zk.x + zm.x) * (R)0.5, (zk.y + zm.y) * (R)0.5);
-    const C D = mk<C>((zk.x - zm.x) * (R)0.5, (zk.y - zm.y) * (R)0.5);
-    const C B = mk<C>(D.y, -D.x);
-    if (ra < nrows) spec[ra * Hp + k] = A;
-    if (rb < nrows) spec[rb * Hp + k] = B;
-  }
+// Generic kernels (bodies in ops_prec.cuh): lengths with factors 3, 5, 7 or
+// below 16, and every transform of a recorded (persistent) solve.
+template <typename R> __global__ void __launch_bounds__(512) k_prec_rows_fwd(PrecRowsArgs<R> a) {
+  PrecRowsFwdOp<R>::template run<false>(hw_ctx(), a);
 }
-
-// Step 5: half spectra -> rows of z.
-template <typename R>
-__global__ void __launch_bounds__(512) k_prec_rows_inv(const cplx<R>* __restrict__ spec, R* __restrict__ z,
-                                                        long long nrows, int n, int H, int Hp,
-                                                        const cplx<R>* __restrict__ twn, FftPlan pl, int pairs, Gate gate) {
-  if (gate_closed(gate)) return;
-  using C = cplx<R>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  const long long row0 = (long long)blockIdx.x * pairs * 2;
-  for (int e = threadIdx.x; e < pairs * n; e += blockDim.x) {
-    const int p = e / n, k = e - p * n;
-    const long long ra = row0 + 2 * p, rb = ra + 1;
-    const bool lo = k < H;
-    const int kk = lo ? k : n - k;
-    C A = ra < nrows ? spec[ra * Hp + kk] : mk<C>(0, 0);
-    C B = rb < nrows ? spec[rb * Hp + kk] : mk<C>(0, 0);
-    if (!lo) {
-      A = cconj(A);
-      B = cconj(B);
-    }
-    buf[p * n + k] = mk<C>(A.x - B.y, A.y + B.x);  // A + i B
-  }
-  __syncthreads();
-  smem_fft<R, kPEPT>(buf, pairs, n, pl, twn, true);
-  for (int e = threadIdx.x; e < pairs * n; e += blockDim.x) {
-    const int p = e / n, j = e - p * n;
-    const long long ra = row0 + 2 * p, rb = ra + 1;
-    const C v = buf[p * n + j];
-    if (ra < nrows) z[ra * n + j] = v.x;
-    if (rb < nrows) z[rb * n + j] = v.y;
-  }
+template <typename R> __global__ void __launch_bounds__(512) k_prec_rows_inv(PrecRowsArgs<R> a) {
+  PrecRowsInvOp<R>::template run<false>(hw_ctx(), a);
 }
-
-// Steps 2-4: complex columns of spec along an axis (x1: stride Hp inside each
-// time slice; t: stride nx*Hp). mode: 0 forward, 1 inverse, 2 forward, divide
-// by sigma*N (or |Lambda|^2 * N), inverse.
-struct DivArgs {
-  int divide;     // 1 on the time pass
-  int adjoint;    // 1: sigma = |Lambda|^2
-  double m1, inv_m2, psi, inv_N;
-  double cre;     // matching approximation: sigma += cre Re(Lambda) (0: S-tilde)
-  int Hp, H;
-  Gate gate;  // device-side skip of the launch (host-sync-free solve)
-};
-
-template <typename R>
-__global__ void __launch_bounds__(1024) k_prec_axis(cplx<R>* __restrict__ spec, int n, long long axis_stride,
-                                                     long long n_inner, long long outer_stride, long long n_outer,
-                                                     const cplx<R>* __restrict__ twn, FftPlan pl, int inverse,
-                                                     int lines, DivArgs dv, const cplx<R>* __restrict__ lt,
-                                                     const cplx<R>* __restrict__ lx, const cplx<R>* __restrict__ ly) {
-  if (gate_closed(dv.gate)) return;
-  using C = cplx<R>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  const long long total = n_outer * n_inner;
-  const long long l0 = (long long)blockIdx.x * lines;
-  for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
-    const int a = e / lines, l = e - a * lines;
-    const long long q = l0 + l;
-    C v = mk<C>(0, 0);
-    if (q < total) {
-      const long long o = q / n_inner, c = q - o * n_inner;
-      v = spec[o * outer_stride + c + a * axis_stride];
-    }
-    buf[l * n + a] = v;
-  }
-  __syncthreads();
-  smem_fft<R, kPEPT>(buf, lines, n, pl, twn, dv.divide ? false : (inverse != 0));
-  if (dv.divide) {
-    for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
-      const int l = e / n, k = e - l * n;
-      const long long q = l0 + l;
-      if (q >= total) continue;
-      const long long c = q % n_inner;  // = i*Hp + j within a time slice
-      const int i = (int)(c / dv.Hp), j = (int)(c - (long long)i * dv.Hp);
-      if (j >= dv.H) continue;  // padding column: stays zero
-      const C a = __ldg(&lt[k]), b = __ldg(&lx[i]), d = __ldg(&ly[j]);
-      const R lr = (R)dv.psi * (a.x - b.x - d.x);
-      const R li = (R)dv.psi * (a.y - b.y - d.y);
-      const R mag = lr * lr + li * li;
-      const R sigma = dv.adjoint ? mag : (R)dv.m1 + mag * (R)dv.inv_m2 + (R)dv.cre * lr;
-      const R s = (R)dv.inv_N / sigma;
-      buf[e] = cscale(buf[e], s);
-    }
-    __syncthreads();
-    smem_fft<R, kPEPT>(buf, lines, n, pl, twn, true);
-  }
-  for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
-    const int a = e / lines, l = e - a * lines;
-    const long long q = l0 + l;
-    if (q >= total) continue;
-    const long long o = q / n_inner, c = q - o * n_inner;
-    spec[o * outer_stride + c + a * axis_stride] = buf[l * n + a];
-  }
+template <typename R> __global__ void __launch_bounds__(1024) k_prec_axis(PrecAxisArgs<R> a) {
+  PrecAxisOp<R>::template run<false>(hw_ctx(), a);
 }
 
 template <typename R>
@@ -178,25 +57,25 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
   const long long nrows = (long long)P->nt * P->nx;
   const int ny = P->ny, H = P->H, Hp = P->Hp;
   cudaError_t err;
-  const bool rows_pow2 = ny >= 16 && (ny & (ny - 1)) == 0;
+  const bool rec = recording();
+  const bool rows_pow2 = ny >= 16 && (ny & (ny - 1)) == 0 && !rec;
   // 1. rows forward
   if (rows_pow2) {
     if ((err = launch_prec_rows_reg<R>(ny, 0, r, nullptr, spec, nrows, H, Hp, ptables<R>(Ay).twn, st, gate)) !=
         cudaSuccess)
       return err;
   } else {
-    const int threads = (ny > kPEPT * 256) ? 512 : 256;
+    const int threads = rec ? kPersistThreads : (ny > kPEPT * 256) ? 512 : 256;
     int pairs = (kPEPT * threads) / ny;
     if (pairs < 1) pairs = 1;
     const long long np = (nrows + 1) / 2;
     if (pairs > np) pairs = (int)np;
     const long long grid = (np + pairs - 1) / pairs;
-    k_prec_rows_fwd<R><<<(unsigned)grid, threads, (size_t)pairs * ny * sizeof(C), st>>>(
-        r, spec, nrows, ny, H, Hp, ptables<R>(Ay).twn, Ay.plann, pairs, gate);
-  note_launches(1);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    err = launch_op<PrecRowsFwdOp<R>>(k_prec_rows_fwd<R>, (unsigned)grid, threads, (size_t)pairs * ny * sizeof(C), st,
+                                      {r, nullptr, spec, nrows, ny, H, Hp, ptables<R>(Ay).twn, Ay.plann, pairs, gate});
+    if (err != cudaSuccess) return err;
   }
-  const int threads = sizeof(R) == 4 ? 1024 : 512;
+  const int threads = rec ? kPersistThreads : (sizeof(R) == 4 ? 1024 : 512);
   const int cap = kPEPT * threads;
   DivArgs none{};
   none.gate = gate;
@@ -234,7 +113,7 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
       dv.Hp = Hp;
       dv.H = H;
     }
-    const bool pow2 = n >= 16 && (n & (n - 1)) == 0;
+    const bool pow2 = n >= 16 && (n & (n - 1)) == 0 && !rec;
     if (pow2) {
       err = launch_prec_axis_reg<R>(n, spec, axis_stride, n_inner, outer_stride, n_outer, ptables<R>(A).twn,
                                     tpass ? 2 : (step == 2 ? 1 : 0), dv, ptables<R>(At).lam, ptables<R>(Ax).lam,
@@ -242,11 +121,11 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
       if (err != cudaSuccess) return err;
       continue;
     }
-    k_prec_axis<R><<<(unsigned)grid, threads, (size_t)lines * n * sizeof(C), st>>>(
-        spec, n, axis_stride, n_inner, outer_stride, n_outer, ptables<R>(A).twn, A.plann, step == 2 ? 1 : 0, lines,
-        dv, ptables<R>(At).lam, ptables<R>(Ax).lam, ptables<R>(Ay).lam);
-  note_launches(1);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    err = launch_op<PrecAxisOp<R>>(k_prec_axis<R>, (unsigned)grid, threads, (size_t)lines * n * sizeof(C), st,
+                                   {spec, n, axis_stride, n_inner, outer_stride, n_outer, ptables<R>(A).twn, A.plann,
+                                    step == 2 ? 1 : 0, lines, dv, ptables<R>(At).lam, ptables<R>(Ax).lam,
+                                    ptables<R>(Ay).lam});
+    if (err != cudaSuccess) return err;
   }
   // 5. rows inverse
   if (rows_pow2) {
@@ -254,16 +133,16 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
         cudaSuccess)
       return err;
   } else {
-    const int threads2 = (ny > kPEPT * 256) ? 512 : 256;
+    const int threads2 = rec ? kPersistThreads : (ny > kPEPT * 256) ? 512 : 256;
     int pairs = (kPEPT * threads2) / ny;
     if (pairs < 1) pairs = 1;
     const long long np = (nrows + 1) / 2;
     if (pairs > np) pairs = (int)np;
     const long long grid = (np + pairs - 1) / pairs;
-    k_prec_rows_inv<R><<<(unsigned)grid, threads2, (size_t)pairs * ny * sizeof(C), st>>>(
-        spec, z, nrows, ny, H, Hp, ptables<R>(Ay).twn, Ay.plann, pairs, gate);
-  note_launches(1);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    err = launch_op<PrecRowsInvOp<R>>(k_prec_rows_inv<R>, (unsigned)grid, threads2, (size_t)pairs * ny * sizeof(C),
+                                      st, {nullptr, z, spec, nrows, ny, H, Hp, ptables<R>(Ay).twn, Ay.plann, pairs,
+                                           gate});
+    if (err != cudaSuccess) return err;
   }
   return cudaSuccess;
 }

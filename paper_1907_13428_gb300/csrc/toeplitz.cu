@@ -20,111 +20,17 @@
 // B^T) is folded into the x1 pass; for alpha_t < 1 a third pass applies the
 // lower-triangular Toeplitz C_t along t (stride nx*ny) by the same embedding.
 
-#include "toeplitz.cuh"
+#include "ops_fft.cuh"
 
 namespace fde {
-// ---------------------------------------------------------------------------
-// x2 axis: rows of n contiguous values; a CTA takes `pairs` row pairs and
-// builds 2*pairs complex lines of length L (pair p, half s -> line 2p+s).
-// ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(512) k_rows(const R* __restrict__ x, long long nrows, int n, int L,
-                                               const cplx<R>* __restrict__ sym, const cplx<R>* __restrict__ tw2,
-                                               const cplx<R>* __restrict__ twL, FftPlan pl, int conj_sym, int pairs,
-                                               AxisEpi<R> E) {
-  if (gate_closed(E.gate)) return;
-  using C = cplx<R>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  const long long row0 = (long long)blockIdx.x * pairs * 2;
-  const int nl = 2 * pairs;
-  for (int e = threadIdx.x; e < pairs * L; e += blockDim.x) {
-    const int p = e / L, j = e - p * L;
-    const long long ra = row0 + 2 * p, rb = ra + 1;
-    R a = 0, b = 0;
-    if (j < n) {
-      if (ra < nrows) a = x[ra * n + j];
-      if (rb < nrows) b = x[rb * n + j];
-    }
-    const C v = mk<C>(a, b);
-    buf[(2 * p) * L + j] = v;
-    buf[(2 * p + 1) * L + j] = (j < n) ? cmul(v, __ldg(&tw2[j])) : mk<C>(0, 0);
-  }
-  __syncthreads();
-  smem_fft<R, kEPT>(buf, nl, L, pl, twL, false);
-  for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
-    const int l = e / L, k = e - l * L;
-    C w = __ldg(&sym[(l & 1) * L + k]);
-    if (conj_sym) w.y = -w.y;
-    buf[e] = cmul(buf[e], w);
-  }
-  __syncthreads();
-  smem_fft<R, kEPT>(buf, nl, L, pl, twL, true);
-  for (int e = threadIdx.x; e < pairs * n; e += blockDim.x) {
-    const int p = e / n, j = e - p * n;
-    const long long ra = row0 + 2 * p, rb = ra + 1;
-    const C v = cadd(buf[(2 * p) * L + j], cmul(buf[(2 * p + 1) * L + j], cconj(__ldg(&tw2[j]))));
-    if (ra < nrows) axis_store(E, ra * n + j, (int)(ra / E.rows_per_slice), v.x);
-    if (rb < nrows) axis_store(E, rb * n + j, (int)(rb / E.rows_per_slice), v.y);
-  }
+// Generic passes (bodies in ops_fft.cuh): lengths below 16 or with factors 3, 5,
+// 7, and every pass of a recorded (persistent) solve.
+template <typename R> __global__ void __launch_bounds__(512) k_rows(RowsArgs<R> a) {
+  RowsOp<R>::template run<false>(hw_ctx(), a);
 }
-
-// ---------------------------------------------------------------------------
-// Strided axis: line (o, c) reads x[o*outer_stride + c + a*axis_stride],
-// a in [0, n); inner indices c are taken in pairs (c, c+1) packed as one
-// complex line. A CTA takes `pairs` consecutive pairs (inner fastest).
-// ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(1024) k_axis(const R* __restrict__ x, int n, int L, long long axis_stride,
-                                                long long n_inner, long long outer_stride, long long n_outer,
-                                                const cplx<R>* __restrict__ sym, const cplx<R>* __restrict__ tw2,
-                                                const cplx<R>* __restrict__ twL, FftPlan pl, int conj_sym,
-                                                int pairs, AxisEpi<R> E) {
-  if (gate_closed(E.gate)) return;
-  using C = cplx<R>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  const long long npi = (n_inner + 1) / 2;
-  const long long total = n_outer * npi;
-  const long long q0 = (long long)blockIdx.x * pairs;
-  const int nl = 2 * pairs;
-  for (int e = threadIdx.x; e < pairs * L; e += blockDim.x) {
-    const int a = e / pairs, p = e - a * pairs;
-    const long long q = q0 + p;
-    R va = 0, vb = 0;
-    if (q < total && a < n) {
-      const long long o = q / npi, c = 2 * (q - o * npi);
-      const long long idx = o * outer_stride + c + a * axis_stride;
-      va = x[idx];
-      if (c + 1 < n_inner) vb = x[idx + 1];
-    }
-    const C v = mk<C>(va, vb);
-    buf[(2 * p) * L + a] = v;
-    buf[(2 * p + 1) * L + a] = (a < n) ? cmul(v, __ldg(&tw2[a])) : mk<C>(0, 0);
-  }
-  __syncthreads();
-  smem_fft<R, kEPT>(buf, nl, L, pl, twL, false);
-  for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
-    const int l = e / L, k = e - l * L;
-    C w = __ldg(&sym[(l & 1) * L + k]);
-    if (conj_sym) w.y = -w.y;
-    buf[e] = cmul(buf[e], w);
-  }
-  __syncthreads();
-  smem_fft<R, kEPT>(buf, nl, L, pl, twL, true);
-  for (int e = threadIdx.x; e < pairs * n; e += blockDim.x) {
-    const int a = e / pairs, p = e - a * pairs;
-    const long long q = q0 + p;
-    if (q >= total) continue;
-    const long long o = q / npi, c = 2 * (q - o * npi);
-    const long long idx = o * outer_stride + c + a * axis_stride;
-    const C v = cadd(buf[(2 * p) * L + a], cmul(buf[(2 * p + 1) * L + a], cconj(__ldg(&tw2[a]))));
-    const int t = E.t_is_axis ? a : (int)o;
-    axis_store(E, idx, t, v.x);
-    if (c + 1 < n_inner) axis_store(E, idx + 1, t, v.y);
-  }
+template <typename R> __global__ void __launch_bounds__(1024) k_axis(AxisArgs<R> a) {
+  AxisOp<R>::template run<false>(hw_ctx(), a);
 }
-
 
 template <typename R> static const AxisTables<R>& tables(const Axis& A);
 template <> const AxisTables<double>& tables<double>(const Axis& A) { return A.d; }
@@ -155,8 +61,9 @@ static cudaError_t launch_rows(fde_problem* P, const R* x, int conj_sym, const c
   const Axis& A = P->ax[2];
   const AxisTables<R>& T = tables<R>(A);
   const int L = A.L;
-  if (L >= 16) return launch_rows_reg<R, R>(P, x, conj_sym, sym ? sym : T.sym, T, E, st);
-  const int threads = rows_threads<R>(L);
+  const bool rec = recording();
+  if (L >= 16 && !rec) return launch_rows_reg<R, R>(P, x, conj_sym, sym ? sym : T.sym, T, E, st);
+  const int threads = rec ? kPersistThreads : rows_threads<R>(L);
   const int cap = kEPT * threads;  // complex elements per CTA
   int pairs = cap / (2 * L);
   if (pairs < 1) pairs = 1;
@@ -165,10 +72,8 @@ static cudaError_t launch_rows(fde_problem* P, const R* x, int conj_sym, const c
   if (pairs > npairs) pairs = (int)npairs;
   const long long grid = (npairs + pairs - 1) / pairs;
   const size_t smem = (size_t)2 * pairs * L * sizeof(cplx<R>);
-  k_rows<R><<<(unsigned)grid, threads, smem, st>>>(x, nrows, A.n, L, sym ? sym : T.sym, T.tw2, T.twL, A.planL,
-                                                   conj_sym, pairs, E);
-  note_launches(1);
-  return cudaGetLastError();
+  return launch_op<RowsOp<R>>(k_rows<R>, (unsigned)grid, threads, smem, st,
+                              {x, nrows, A.n, L, sym ? sym : T.sym, T.tw2, T.twL, A.planL, conj_sym, pairs, E});
 }
 
 template <typename R>
@@ -177,23 +82,23 @@ static cudaError_t launch_axis(fde_problem* P, int axis, const R* x, int conj_sy
   const Axis& A = P->ax[axis];
   const AxisTables<R>& T = tables<R>(A);
   const int L = A.L;
-  const int threads = sizeof(R) == 4 ? 1024 : 512;
+  const bool rec = recording();
+  const int threads = rec ? kPersistThreads : (sizeof(R) == 4 ? 1024 : 512);
   const int cap = kEPT * threads;
   int pairs = cap / (2 * L);
   if (pairs < 1) pairs = 1;
   long long axis_stride, n_inner, outer_stride, n_outer;
   axis_geometry(P, axis, &axis_stride, &n_inner, &outer_stride, &n_outer);
-  if (L >= 16)
+  if (L >= 16 && !rec)
     return launch_axis_reg<R, R>(L, x, A.n, axis_stride, n_inner, outer_stride, n_outer, sym ? sym : T.sym, T,
                                  conj_sym, E, sizeof(R) == 4 ? P->axis_nt32 : P->axis_nt64, st);
   const long long total = n_outer * ((n_inner + 1) / 2);
   if (pairs > total) pairs = (int)total;
   const long long grid = (total + pairs - 1) / pairs;
   const size_t smem = (size_t)2 * pairs * L * sizeof(cplx<R>);
-  k_axis<R><<<(unsigned)grid, threads, smem, st>>>(x, A.n, L, axis_stride, n_inner, outer_stride, n_outer,
-                                                   sym ? sym : T.sym, T.tw2, T.twL, A.planL, conj_sym, pairs, E);
-  note_launches(1);
-  return cudaGetLastError();
+  return launch_op<AxisOp<R>>(k_axis<R>, (unsigned)grid, threads, smem, st,
+                              {x, A.n, L, axis_stride, n_inner, outer_stride, n_outer, sym ? sym : T.sym, T.tw2,
+                               T.twL, A.planL, conj_sym, pairs, E});
 }
 
 // One pass of B (S: storage type, R: transform arithmetic). `shifted`: the x1
@@ -207,6 +112,10 @@ static cudaError_t pass_axis(fde_problem* P, int axis, const S* x, int conj_sym,
     return launch_axis<R>(P, axis, x, conj_sym, shifted ? tables<R>(A).symD : nullptr, E, st);
   } else {
     if (A.L < 16) return launch_axis<S>(P, axis, x, conj_sym, shifted ? tables<S>(A).symD : nullptr, E, st);
+    if (Recorder* r = active_recorder()) {  // no generic double-float pass to record
+      r->error = 1;
+      return cudaSuccess;
+    }
     const AxisTables<R>& T = tables<R>(A);
     long long axis_stride, n_inner, outer_stride, n_outer;
     axis_geometry(P, axis, &axis_stride, &n_inner, &outer_stride, &n_outer);
@@ -222,6 +131,10 @@ static cudaError_t pass_rows(fde_problem* P, const S* x, int conj_sym, const Axi
   } else {
     const Axis& A = P->ax[2];
     if (A.L < 16) return launch_rows<S>(P, x, conj_sym, nullptr, E, st);
+    if (Recorder* r = active_recorder()) {
+      r->error = 1;
+      return cudaSuccess;
+    }
     return launch_rows_reg<R, S>(P, x, conj_sym, tables<R>(A).sym, tables<R>(A), E, st);
   }
 }

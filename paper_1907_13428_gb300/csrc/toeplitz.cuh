@@ -33,26 +33,26 @@ template <typename R> struct AxisEpi {
   Gate gate;      // device-side skip of the whole launch (host-sync-free solve)
 };
 
-template <typename R>
+template <bool PS = false, typename R>
 __device__ __forceinline__ void axis_store(const AxisEpi<R>& E, long long idx, int t, R res) {
   if (E.plain) {
     E.out[idx] = res;
     return;
   }
   R v = res;
-  if (E.acc) v += E.acc[idx];
+  if (E.acc) v += ldv<PS>(E.acc + idx);
   if (E.xt) {
     R nb = 0;
     if (E.tdir > 0) {
-      if (t > 0) nb = E.xt[idx - E.plane];
+      if (t > 0) nb = ldv<PS>(E.xt + idx - E.plane);
     } else {
-      if (t < E.nt - 1) nb = E.xt[idx + E.plane];
+      if (t < E.nt - 1) nb = ldv<PS>(E.xt + idx + E.plane);
     }
-    v += E.nb_only ? -E.ct * nb : E.ct * (E.xt[idx] - nb);
+    v += E.nb_only ? -E.ct * nb : E.ct * (ldv<PS>(E.xt + idx) - nb);
   }
   const bool last = (t == E.nt - 1);
   if (E.has_dsc) v *= last ? E.dsc1 : E.dsc0;
-  if (E.addv) v += (last ? E.addc1 : E.addc0) * E.addv[idx];
+  if (E.addv) v += (last ? E.addc1 : E.addc0) * ldv<PS>(E.addv + idx);
   E.out[idx] = v;
 }
 
