@@ -367,8 +367,10 @@ typedef struct fde_persist_cfg {
   int replay;        /* 0: the persistent kernel; 1: the same recorded launches issued
                         one by one on `stream` (the reference executor of the tests)      */
   int stall_group;   /* test hook, 0: off. k > 0: the first CTA of instance group k - 1
-                        never arrives at its first group barrier, so that every wait of
-                        that group runs out                                               */
+                        (lockstep: of the grid) never arrives at its first barrier, so
+                        that every wait of that group runs out                            */
+  int schedule;      /* 0: lockstep when every instance recorded the same number of
+                        launches (else instance groups); 1: instance groups               */
 } fde_persist_cfg;
 
 /* What a persistent solve ran (HOST struct, filled on return). */
@@ -379,25 +381,32 @@ typedef struct fde_persist_info {
   int ctas_per_sm;        /* resident CTAs per SM of the persistent kernel               */
   int smem_bytes;         /* dynamic shared memory per CTA                               */
   int timeout_group;      /* on FDE_ETIMEOUT: the group whose wait ran out, else -1      */
-  long long timeout_command; /* ... and the index of the command it had finished         */
+  long long timeout_command; /* ... and the last command (lockstep: step) it had finished,
+                                -1 if none                                                 */
+  int schedule;           /* 0: lockstep, 1: instance groups                             */
 } fde_persist_info;
 
 /* The batch solve of fde_batch_admm_solve (same arguments, options and fixed
  * iteration budgets; opts->precision must be FDE_MIXED: the executor has no
  * double-float transforms) run by ONE persistent cooperative kernel.
  * The launches that fde_batch_admm_solve would capture into its graph are
- * recorded instead (every transform in its generic shared-memory form, every
- * launch with 256 threads); the kernel keeps ctas_per_sm x SMs CTAs resident,
+ * recorded instead (every launch with 256 threads: the register-resident float
+ * passes and preconditioner transforms; the double passes and the lines
+ * shorter than 16 in the generic shared-memory transforms); the kernel keeps ctas_per_sm x SMs CTAs resident,
  * split into instance groups of cfg->group_ctas CTAs. A group takes the next
  * instance from a device-side queue (largest instances first), runs the
  * bodies of that instance's recorded launches one after another (each launch's
  * blocks spread over the group's CTAs) with a group barrier after each, and
- * takes the next instance until the queue is empty. Every barrier wait is
+ * takes the next instance until the queue is empty. Lockstep schedule (the
+ * default when every instance recorded the same number of launches, as the
+ * fixed budgets make them): step k runs launch k of every instance, the blocks
+ * of all of them spread over all CTAs, then one barrier of all CTAs; instances
+ * of very different sizes then share the whole GPU. Every barrier wait is
  * bounded by cfg->timeout_s: when one runs out the kernel records the group
  * and command, every CTA returns within about one more limit, and the call
  * returns FDE_ETIMEOUT with the context usable. cfg may be NULL (defaults);
  * info may be NULL. Every axis length (nx, ny, nt) must be a power of two
- * (the executor's transforms are the radix-4/2 ones) and at most 2048.
+ * (the executor holds the power-of-two transforms of lengths up to 2048).
  * Synchronises `stream`. Errors: FDE_EINVAL (as fde_batch_admm_solve;
  * precision not FDE_MIXED; a negative cfg field), FDE_EUNSUPPORTED (an axis
  * that is not a power of two or above 2048, a command the executor cannot

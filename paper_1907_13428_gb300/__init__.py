@@ -53,13 +53,13 @@ class fde_admm_stats(ctypes.Structure):
 
 class fde_persist_cfg(ctypes.Structure):
     _fields_ = [("group_ctas", ctypes.c_int), ("timeout_s", ctypes.c_double), ("replay", ctypes.c_int),
-                ("stall_group", ctypes.c_int)]
+                ("stall_group", ctypes.c_int), ("schedule", ctypes.c_int)]
 
 
 class fde_persist_info(ctypes.Structure):
     _fields_ = [("commands", ctypes.c_longlong), ("groups", ctypes.c_int), ("group_ctas", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("smem_bytes", ctypes.c_int), ("timeout_group", ctypes.c_int),
-                ("timeout_command", ctypes.c_longlong)]
+                ("timeout_command", ctypes.c_longlong), ("schedule", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -449,12 +449,13 @@ class Batch:
 
     def admm_solve_persistent(self, opts: AdmmOptions, ybars, ya=None, yb=None, ua=None, ub=None, out=None,
                               group_ctas: int = 0, timeout_s: float = 0.0, replay: bool = False,
-                              stall_group: int = 0, check: bool = True):
+                              stall_group: int = 0, schedule: int = 0, check: bool = True):
         """The same batch solve run by one persistent cooperative kernel
-        (fde_batch_admm_solve_persistent; FDE_MIXED only). replay=True issues the
-        recorded launches one by one instead (reference executor). Returns
-        (ys, us, stats list, info dict, status); with check=True a failing status
-        raises FdeError."""
+        (fde_batch_admm_solve_persistent; FDE_MIXED only). schedule 0: lockstep
+        over the instances, 1: instance groups of group_ctas CTAs taking
+        instances from a queue. replay=True issues the recorded launches one by
+        one instead (reference executor). Returns (ys, us, stats list, info dict,
+        status); with check=True a failing status raises FdeError."""
         n = len(self.sizes)
         if out is None:
             if self._out is None:
@@ -472,7 +473,7 @@ class Batch:
 
         st = (fde_admm_stats * n)()
         info = fde_persist_info()
-        cfg = fde_persist_cfg(int(group_ctas), float(timeout_s), int(bool(replay)), int(stall_group))
+        cfg = fde_persist_cfg(int(group_ctas), float(timeout_s), int(bool(replay)), int(stall_group), int(schedule))
         o = opts.c()
         s = lib().fde_batch_admm_solve_persistent(self._h, ctypes.byref(o), yb_ptrs, arr(ya), arr(yb), arr(ua),
                                                   arr(ub), y_ptrs, u_ptrs, ctypes.byref(cfg), st,

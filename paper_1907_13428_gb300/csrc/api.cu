@@ -1279,6 +1279,8 @@ struct fde_batch {
   size_t rec_smem = 0;
   unsigned char* d_cmds = nullptr;  // device copy of the commands
   long long* d_off = nullptr;
+  int rec_steps = 0;                // launches per instance when all are alike (lockstep), else 0
+  int* d_vstart = nullptr;          // lockstep: [steps][count + 1] prefix sums of the grids
   int* d_order = nullptr;
   void* d_state = nullptr;  // barrier counters, queue, slots, status
   int state_groups = 0;
@@ -1300,6 +1302,7 @@ void fde_batch_destroy(fde_batch* b) {
   if (b->d_off) cudaFree(b->d_off);
   if (b->d_order) cudaFree(b->d_order);
   if (b->d_state) cudaFree(b->d_state);
+  if (b->d_vstart) cudaFree(b->d_vstart);
   delete[] b->probs;
   delete[] b->streams;
   delete[] b->joins;
@@ -1453,7 +1456,9 @@ int fde_batch_admm_solve_persistent(fde_batch* b, const fde_admm_opts* o, const 
   }
   if (!b || !valid_opts(o) || !ybar || !y || !u) return FDE_EINVAL;
   if (o->precision != FDE_MIXED || o->max_admm < 1 || o->max_pcg < 1) return FDE_EINVAL;
-  if (cfg && (cfg->group_ctas < 0 || !(cfg->timeout_s >= 0.0) || cfg->stall_group < 0)) return FDE_EINVAL;
+  if (cfg && (cfg->group_ctas < 0 || !(cfg->timeout_s >= 0.0) || cfg->stall_group < 0 || cfg->schedule < 0 ||
+              cfg->schedule > 1))
+    return FDE_EINVAL;
   const int n = b->count;
   for (int i = 0; i < n; ++i) {
     if (!valid_opts_for(b->probs[i], o)) return FDE_EINVAL;
@@ -1462,9 +1467,8 @@ int fde_batch_admm_solve_persistent(fde_batch* b, const fde_admm_opts* o, const 
   if (o->inner_solver != 0 || o->warm_start || o->inner_x0) return FDE_EUNSUPPORTED;
   auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
   for (int i = 0; i < n; ++i) {
-    // the generic passes of a 256-thread block hold at least one line pair of 2L;
-    // the executor's transforms are the power-of-two ones (the preconditioner
-    // transforms the exact axis lengths)
+    // the executor holds the power-of-two transforms of lengths up to 2048 (the
+    // preconditioner transforms the exact axis lengths)
     const fde_problem* P = b->probs[i];
     if (P->ax[1].L > 2048 || P->ax[2].L > 2048 || (!P->euler && P->ax[0].L > 2048)) return FDE_EUNSUPPORTED;
     if (!pow2(P->nx) || !pow2(P->ny) || !pow2(P->nt)) return FDE_EUNSUPPORTED;
@@ -1513,12 +1517,39 @@ int fde_batch_admm_solve_persistent(fde_batch* b, const fde_admm_opts* o, const 
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->probs[a]->N > b->probs[c]->N; });
+    // lockstep table: equal launch counts, prefix sums of the grids of each step
+    const long long steps = n > 0 ? off[1] - off[0] : 0;
+    bool alike = steps > 0 && steps < (1LL << 30);
+    for (int i = 0; i < n && alike; ++i) alike = off[i + 1] - off[i] == steps;
+    std::vector<int> vstart;
+    if (alike) {
+      vstart.assign((size_t)steps * (n + 1), 0);
+      for (long long k = 0; k < steps && alike; ++k) {
+        long long acc = 0;
+        for (int i = 0; i < n; ++i) {
+          CmdHeader h;
+          std::memcpy(&h, rec.cmds.data() + (off[i] + k) * kCmdBytes, sizeof(h));
+          vstart[k * (n + 1) + i] = (int)acc;
+          acc += h.grid;
+        }
+        vstart[k * (n + 1) + n] = (int)acc;
+        alike = acc < (1LL << 31);
+      }
+    }
     if (b->d_cmds) cudaFree(b->d_cmds);
     if (b->d_off) cudaFree(b->d_off);
     if (b->d_order) cudaFree(b->d_order);
+    if (b->d_vstart) cudaFree(b->d_vstart);
     b->d_cmds = nullptr;
     b->d_off = nullptr;
     b->d_order = nullptr;
+    b->d_vstart = nullptr;
+    b->rec_steps = 0;
+    if (alike) {
+      if (cudaMalloc(&b->d_vstart, sizeof(int) * vstart.size()) != cudaSuccess) return FDE_ENOMEM;
+      CK(cudaMemcpy(b->d_vstart, vstart.data(), sizeof(int) * vstart.size(), cudaMemcpyHostToDevice));
+      b->rec_steps = (int)steps;
+    }
     if (cudaMalloc(&b->d_cmds, rec.cmds.size()) != cudaSuccess ||
         cudaMalloc(&b->d_off, sizeof(long long) * (n + 1)) != cudaSuccess ||
         cudaMalloc(&b->d_order, sizeof(int) * n) != cudaSuccess)
@@ -1544,7 +1575,8 @@ int fde_batch_admm_solve_persistent(fde_batch* b, const fde_admm_opts* o, const 
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (cps < 1) return FDE_EUNSUPPORTED;
   const int total = cps * sms;
-  int gc = (cfg && cfg->group_ctas > 0) ? cfg->group_ctas : total / std::min(16, n);
+  const bool lockstep = b->rec_steps > 0 && !(cfg && cfg->schedule == 1);
+  int gc = lockstep ? total : (cfg && cfg->group_ctas > 0) ? cfg->group_ctas : total / std::min(16, n);
   gc = std::max(1, std::min(gc, total));
   const int groups = total / gc;
   if (info) {
@@ -1553,6 +1585,7 @@ int fde_batch_admm_solve_persistent(fde_batch* b, const fde_admm_opts* o, const 
     info->group_ctas = gc;
     info->ctas_per_sm = cps;
     info->smem_bytes = (int)b->rec_smem;
+    info->schedule = lockstep ? 0 : 1;
   }
   if (cfg && cfg->replay) {
     CK(fde::persist_replay(b->rec_cmds.data(), ncmd, st));
@@ -1582,6 +1615,8 @@ int fde_batch_admm_solve_persistent(fde_batch* b, const fde_admm_opts* o, const 
     const double lim = (cfg && cfg->timeout_s > 0.0) ? cfg->timeout_s : 1.0;
     pl.timeout_ns = (unsigned long long)(lim * 1e9);
     pl.stall_group = (cfg && cfg->stall_group > 0) ? cfg->stall_group - 1 : -1;
+    pl.steps = lockstep ? b->rec_steps : 0;
+    pl.vstart = b->d_vstart;
     CK(fde::persist_run(pl, b->rec_smem, st));
     CK(cudaStreamSynchronize(st));
     long long hs[4];

@@ -25,7 +25,7 @@ template <typename R> struct RowsArgs {
 };
 template <typename R> struct RowsOp {
   using Args = RowsArgs<R>;
-  template <bool PS> __device__ static void run(const Ctx& c, const Args& a) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& c, const Args& a) {
     if (gate_closed<PS>(a.E.gate)) return;
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -85,7 +85,7 @@ template <typename R> struct AxisArgs {
 };
 template <typename R> struct AxisOp {
   using Args = AxisArgs<R>;
-  template <bool PS> __device__ static void run(const Ctx& cx, const Args& g) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& cx, const Args& g) {
     if (gate_closed<PS>(g.E.gate)) return;
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -34,7 +34,7 @@ template <typename R> struct PrecRowsArgs {
 };
 template <typename R> struct PrecRowsFwdOp {
   using Args = PrecRowsArgs<R>;
-  template <bool PS> __device__ static void run(const Ctx& c, const Args& a) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& c, const Args& a) {
     if (gate_closed<PS>(a.gate)) return;
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -70,7 +70,7 @@ template <typename R> struct PrecRowsFwdOp {
 // Step 5: half spectra -> rows of z.
 template <typename R> struct PrecRowsInvOp {
   using Args = PrecRowsArgs<R>;
-  template <bool PS> __device__ static void run(const Ctx& c, const Args& a) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& c, const Args& a) {
     if (gate_closed<PS>(a.gate)) return;
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -121,7 +121,7 @@ template <typename R> struct PrecAxisArgs {
 };
 template <typename R> struct PrecAxisOp {
   using Args = PrecAxisArgs<R>;
-  template <bool PS> __device__ static void run(const Ctx& cx, const Args& g) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& cx, const Args& g) {
     const DivArgs& dv = g.dv;
     if (gate_closed<PS>(dv.gate)) return;
     using C = cplx<R>;

@@ -93,7 +93,7 @@ template <typename RA, typename RB> struct DotArgs {
 };
 template <typename RA, typename RB> struct DotOp {
   using Args = DotArgs<RA, RB>;
-  template <bool PS> __device__ static void run(const Ctx& c, const Args& p) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& c, const Args& p) {
     __shared__ double sh[32];
     Acc<RA> acc;
     for (long long i = gs_first(c); i < p.n; i += gs_step(c)) acc.add(ldv<PS>(p.a + i) * ldv<PS>(p.b + i));
@@ -116,7 +116,7 @@ struct FinishArgs {
 };
 struct FinishSumOp {
   using Args = FinishArgs;
-  template <bool PS> __device__ static void run(const Ctx&, const Args& p) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx&, const Args& p) {
     __shared__ double sh[32];
     double s = 0.0;
     for (int i = threadIdx.x; i < p.np; i += blockDim.x) s += ldv<PS>(p.partials + i);
@@ -174,7 +174,7 @@ template <typename RV> struct PcgXrArgs {
 };
 template <typename RV> struct PcgXrOp {
   using Args = PcgXrArgs<RV>;
-  template <bool PS> __device__ static void run(const Ctx& c, const Args& p) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& c, const Args& p) {
     __shared__ double sh[32];
     const RV alpha = (RV)ldv<PS>(p.dscal + S_ALPHA);
     Acc<RV> acc;
@@ -198,7 +198,7 @@ template <typename RV> struct PcgPArgs {
 };
 template <typename RV> struct PcgPOp {
   using Args = PcgPArgs<RV>;
-  template <bool PS> __device__ static void run(const Ctx& c, const Args& p) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& c, const Args& p) {
     const RV beta = (RV)ldv<PS>(p.dscal + S_BETA);
     for (long long i = gs_first(c); i < p.n; i += gs_step(c)) p.d[i] = ldv<PS>(p.z + i) + beta * ldv<PS>(p.d + i);
   }
@@ -212,7 +212,7 @@ struct ToF32Args {
 };
 struct ToF32Op {
   using Args = ToF32Args;
-  template <bool PS> __device__ static void run(const Ctx& c, const Args& p) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& c, const Args& p) {
     for (long long i = gs_first(c); i < p.n; i += gs_step(c)) p.out[i] = (float)ldv<PS>(p.in + i);
   }
 };
@@ -226,7 +226,7 @@ struct ToF32UnlessArgs {
 };
 struct ToF32UnlessOp {
   using Args = ToF32UnlessArgs;
-  template <bool PS> __device__ static void run(const Ctx& c, const Args& p) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& c, const Args& p) {
     const bool conv = ldv<PS>(p.dscal + S_CONV) != 0.0;
     for (long long i = gs_first(c); i < p.n; i += gs_step(c)) p.out[i] = conv ? 0.f : (float)ldv<PS>(p.in + i);
   }
@@ -241,7 +241,7 @@ struct AddF32UnlessArgs {
 };
 struct AddF32UnlessOp {
   using Args = AddF32UnlessArgs;
-  template <bool PS> __device__ static void run(const Ctx& c, const Args& p) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& c, const Args& p) {
     if (ldv<PS>(p.dscal + S_CONV) != 0.0) return;
     for (long long i = gs_first(c); i < p.n; i += gs_step(c)) p.y[i] = ldv<PS>(p.y + i) + (double)ldv<PS>(p.d + i);
   }
@@ -255,7 +255,7 @@ struct ScalarStepArgs {
 };
 struct ScalarStepOp {
   using Args = ScalarStepArgs;
-  template <bool PS> __device__ static void run(const Ctx& c, const Args& p) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& c, const Args& p) {
     if (threadIdx.x != 0 || c.bid != 0) return;
     double* d = p.dscal;
     if (p.op == 0) d[p.dst] = fmax(ldv<PS>(d + p.dst), ldv<PS>(d + p.src));
@@ -270,7 +270,7 @@ template <typename R> struct FillArgs {
 };
 template <typename R> struct FillOp {
   using Args = FillArgs<R>;
-  template <bool PS> __device__ static void run(const Ctx& c, const Args& p) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& c, const Args& p) {
     for (long long i = gs_first(c); i < p.n; i += gs_step(c)) p.x[i] = p.v;
   }
 };
@@ -282,7 +282,7 @@ template <typename R> struct CopyArgs {
 };
 template <typename R> struct CopyOp {
   using Args = CopyArgs<R>;
-  template <bool PS> __device__ static void run(const Ctx& c, const Args& p) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& c, const Args& p) {
     for (long long i = gs_first(c); i < p.n; i += gs_step(c)) p.dst[i] = ldv<PS>(p.src + i);
   }
 };
@@ -304,7 +304,7 @@ struct AdmmPreArgs {
 };
 struct AdmmPreOp {
   using Args = AdmmPreArgs;
-  template <bool PS> __device__ static void run(const Ctx& cx, const Args& a) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& cx, const Args& a) {
     const AdmmArgs& A = a.A;
     // Coefficients folded once per thread: on this GPU the double pipe, not memory,
     // bounds these streaming steps, so each element costs fused multiply-adds only
@@ -351,7 +351,7 @@ struct AdmmPostArgs {
 };
 struct AdmmPostOp {
   using Args = AdmmPostArgs;
-  template <bool PS> __device__ static void run(const Ctx& cx, const Args& a) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& cx, const Args& a) {
     __shared__ double sh[32];
     __shared__ long long shl[32];
     const AdmmArgs& A = a.A;
@@ -419,7 +419,7 @@ struct AdmmFinishArgs {
 };
 struct AdmmFinishOp {
   using Args = AdmmFinishArgs;
-  template <bool PS> __device__ static void run(const Ctx&, const Args& p) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx&, const Args& p) {
     __shared__ double sh[32];
     double a = 0.0, b = 0.0, c = 0.0, o = 0.0, f = 0.0;
     const int np = p.np;
@@ -456,7 +456,7 @@ struct FoldArgs {
 };
 struct FoldOp {
   using Args = FoldArgs;
-  template <bool PS> __device__ static void run(const Ctx& cx, const Args& a) {
+  template <bool PS> static __device__ __forceinline__ void run(const Ctx& cx, const Args& a) {
     for (long long i = gs_first(cx); i < a.n; i += gs_step(cx)) {
       const bool last = i >= a.last_start;
       a.v[i] = ldv<PS>(a.q + i) - (last ? a.m2inv1 : a.m2inv0) * ldv<PS>(a.t + i);

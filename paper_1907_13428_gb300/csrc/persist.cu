@@ -11,6 +11,13 @@
 // b mod group size), with a group barrier after each launch. Instances are
 // independent, so groups never wait on each other.
 //
+// Lockstep schedule: when every instance recorded the same number of launches
+// (the batch solve's fixed budgets make the sequences alike), step k runs launch
+// k of every instance at once: the blocks of those launches form one index
+// space (prefix sums of their grids), spread over all CTAs, followed by one
+// barrier of all CTAs. This balances instances of very different sizes across
+// the whole GPU.
+//
 // Barrier: each CTA's thread 0 fences its block's writes (after a block-wide
 // __syncthreads), adds one to the group's arrival counter and spins with an
 // acquire load until the counter reaches the CTA's own count of arrivals
@@ -19,9 +26,10 @@
 // and its CTA returns; any CTA that sees a recorded failure while waiting
 // returns too, so the kernel ends within about one more limit.
 #include "ops_fft.cuh"
-#include "ops_prec.cuh"
+#include "ops_prec_reg.cuh"
 #include "ops_vec.cuh"
 #include "persist.h"
+#include "toeplitz_reg.cuh"
 
 namespace fde {
 
@@ -31,9 +39,18 @@ Recorder*& active_recorder() {
 }
 
 // One operation's body as a separate (not inlined) function: each body keeps
-// its own register allocation instead of one allocation for all of them.
+// its own register allocation instead of one allocation for all of them. The
+// body works on a private copy of its argument record: the body's stores to
+// global memory could alias the record where it lies, which would make the
+// compiler reload its fields after every store.
 template <class Op> __device__ __noinline__ void run_persistent(const Ctx& c, const unsigned char* args) {
-  Op::template run<true>(c, *reinterpret_cast<const typename Op::Args*>(args));
+  using A = typename Op::Args;
+  static_assert(sizeof(A) % 8 == 0 && alignof(A) <= 8, "argument records are copied in 8-byte words");
+  unsigned long long w[sizeof(A) / 8];
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(args);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(A) / 8); ++i) w[i] = __ldg(src + i);
+  Op::template run<true>(c, *reinterpret_cast<const A*>(w));
 }
 
 template <class List> struct Exec;
@@ -133,16 +150,43 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_persist(PersistLaunch pl
   }
 }
 
+__global__ void __launch_bounds__(kPersistThreads, 2) k_persist_lockstep(PersistLaunch pl) {
+  GroupBarrier bar{pl.bar, 0u, (int)gridDim.x, pl.stall_group == 0 && blockIdx.x == 0};
+  const int n = pl.count;
+  for (int k = 0; k < pl.steps; ++k) {
+    const int* pre = pl.vstart + (long long)k * (n + 1);
+    const long long V = pre[n];
+    for (long long vb = blockIdx.x; vb < V; vb += gridDim.x) {
+      int lo = 0, hi = n;  // largest i with pre[i] <= vb
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= vb) lo = mid;
+        else hi = mid;
+      }
+      const unsigned char* cmd = pl.cmds + (pl.off[lo] + k) * kCmdBytes;
+      const CmdHeader h = *reinterpret_cast<const CmdHeader*>(cmd);
+      PersistExec::run(h.op, Ctx{vb - pre[lo], (long long)h.grid}, cmd + kCmdHeaderBytes);
+    }
+    if (!group_sync(bar, pl, 0, k)) return;
+  }
+}
+
 cudaError_t persist_prepare(size_t smem, int* ctas_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_persist, kPersistThreads, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_persist_lockstep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int a = 0, b = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_persist, kPersistThreads, smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_persist_lockstep, kPersistThreads, smem);
+  *ctas_per_sm = a < b ? a : b;
+  return e;
 }
 
 cudaError_t persist_run(const PersistLaunch& pl, size_t smem, cudaStream_t st) {
   PersistLaunch a = pl;
   void* args[] = {&a};
-  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_persist, dim3((unsigned)(pl.groups * pl.group_ctas)),
+  const void* kern = pl.steps > 0 ? (const void*)k_persist_lockstep : (const void*)k_persist;
+  const cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3((unsigned)(pl.groups * pl.group_ctas)),
                                                     dim3(kPersistThreads), args, smem, st);
   note_launches(1);
   return e;

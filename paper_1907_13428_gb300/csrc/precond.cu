@@ -16,7 +16,7 @@
 //   4. x1 columns: inverse DFT;
 //   5. x2 rows: the two Hermitian half spectra are recombined into one complex
 //      line, inverse DFT, real and imaginary parts are the two output rows.
-#include "ops_prec.cuh"
+#include "ops_prec_reg.cuh"
 
 namespace fde {
 
@@ -57,8 +57,10 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
   const long long nrows = (long long)P->nt * P->nx;
   const int ny = P->ny, H = P->H, Hp = P->Hp;
   cudaError_t err;
+  // a recorded solve: float transforms register-resident (256 threads), double ones generic
+  const bool gen = recording() && sizeof(R) != 4;
   const bool rec = recording();
-  const bool rows_pow2 = ny >= 16 && (ny & (ny - 1)) == 0 && !rec;
+  const bool rows_pow2 = ny >= 16 && (ny & (ny - 1)) == 0 && !gen;
   // 1. rows forward
   if (rows_pow2) {
     if ((err = launch_prec_rows_reg<R>(ny, 0, r, nullptr, spec, nrows, H, Hp, ptables<R>(Ay).twn, st, gate)) !=
@@ -113,7 +115,7 @@ cudaError_t apply_precond(fde_problem* P, double m1, double m2, int mode, const 
       dv.Hp = Hp;
       dv.H = H;
     }
-    const bool pow2 = n >= 16 && (n & (n - 1)) == 0 && !rec;
+    const bool pow2 = n >= 16 && (n & (n - 1)) == 0 && !gen;
     if (pow2) {
       err = launch_prec_axis_reg<R>(n, spec, axis_stride, n_inner, outer_stride, n_outer, ptables<R>(A).twn,
                                     tpass ? 2 : (step == 2 ? 1 : 0), dv, ptables<R>(At).lam, ptables<R>(Ax).lam,
@@ -175,16 +177,9 @@ cudaError_t precond_set_smem_attrs() {
 }  // namespace fde
 
 // ===========================================================================
-// Register-resident column transforms for power-of-two lengths >= 16
-// (fftreg.cuh). Lanes run over columns (coalesced); shared memory is
-// position-major, CP columns per position row, with the physical row
-// pos ^ parity(pos bits 1..4) so that the two position groups of every
-// half-warp (quarter-warp for double) land in different bank halves.
-// mode 0: forward (natural order in, frequency layout out),
-// mode 1: inverse, mode 2: forward, divide by N sigma, inverse.
+// Register-resident column transforms and x2-row transforms for power-of-two
+// lengths >= 16 (bodies in ops_prec_reg.cuh).
 // ===========================================================================
-#include "fftreg.cuh"
-
 namespace fde {
 
 // Plain transforms (modes 0, 1) are compiled for two resident CTAs (at most 64
@@ -192,99 +187,49 @@ namespace fde {
 // and need the warps to hide its latency; the divide pass keeps one CTA.
 template <int MODE> constexpr int prec_min_blocks() { return MODE == 2 ? 1 : 2; }
 
-// 1/sigma: the float pass uses the fast reciprocal (a preconditioner needs no
-// correctly rounded quotient), the double pass the IEEE quotient.
-__device__ __forceinline__ float prec_recip(float s) { return __frcp_rn(s); }
-__device__ __forceinline__ double prec_recip(double s) { return 1.0 / s; }
-
 template <typename R, int L, int NT, int MODE>
-__global__ void __launch_bounds__(NT, prec_min_blocks<MODE>()) k_prec_axis_reg(
-    cplx<R>* __restrict__ spec, long long axis_stride, long long n_inner, long long outer_stride, long long n_outer,
-    const cplx<R>* __restrict__ twn, DivArgs dv, const cplx<R>* __restrict__ lt, const cplx<R>* __restrict__ lx,
-    const cplx<R>* __restrict__ ly) {
-  constexpr int mode = MODE;
-  if (gate_closed(dv.gate)) return;
-  using C = cplx<R>;
-  constexpr int T = L / 16, CP = NT / T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  const int cl = threadIdx.x % CP, t = threadIdx.x / CP;
-  const long long total = n_outer * n_inner;
-  const long long q = (long long)blockIdx.x * CP + cl;
-  const bool valid = q < total;
-  const long long o = valid ? q / n_inner : 0;
-  const long long c = valid ? q - o * n_inner : 0;
-  const long long base = o * outer_stride + c;
-  const FlipLayout<C, CP> lay{sm, cl};
-  C v[1][16];
-  if constexpr (mode == 1) {
-#pragma unroll
-    for (int idx = 0; idx < 16; ++idx) {
-      const int p = rf_freq<L>(t, idx);
-      v[0][idx] = valid ? spec[base + p * axis_stride] : mk<C>(0, 0);
-    }
-    rf_inverse<R, L, 1>(v, t, twn, lay);
-  } else {
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const int p = t + r * T;
-      v[0][r] = valid ? spec[base + p * axis_stride] : mk<C>(0, 0);
-    }
-    rf_forward<R, L, 1>(v, t, twn, lay);
-    if constexpr (mode == 2) {
-      const int i = (int)(c / dv.Hp), j = (int)(c - (long long)i * dv.Hp);
-      const bool pad = j >= dv.H;
-      const C b = pad ? mk<C>(0, 0) : __ldg(&lx[i]);
-      const C d = pad ? mk<C>(0, 0) : __ldg(&ly[j]);
-#pragma unroll
-      for (int idx = 0; idx < 16; ++idx) {
-        const int k = rf_freq<L>(t, idx);
-        // sigma in the arithmetic of the transform (float on the float path:
-        // double divides would run at 1/58 of the float rate)
-        const C a = __ldg(&lt[k]);
-        const R lr = (R)dv.psi * (a.x - b.x - d.x);
-        const R li = (R)dv.psi * (a.y - b.y - d.y);
-        const R mag = lr * lr + li * li;
-        const R sigma = dv.adjoint ? mag : (R)dv.m1 + mag * (R)dv.inv_m2 + (R)dv.cre * lr;
-        const R sc = pad ? (R)0 : (R)dv.inv_N * prec_recip(sigma);
-        v[0][idx] = cscale(v[0][idx], sc);
-      }
-      rf_inverse<R, L, 1>(v, t, twn, lay);
-    }
-  }
-  if (!valid) return;
-  if constexpr (mode == 0) {
-#pragma unroll
-    for (int idx = 0; idx < 16; ++idx) spec[base + rf_freq<L>(t, idx) * axis_stride] = v[0][idx];
-  } else {
-#pragma unroll
-    for (int r = 0; r < 16; ++r) spec[base + (t + r * T) * axis_stride] = v[0][r];
-  }
+__global__ void __launch_bounds__(NT, prec_min_blocks<MODE>()) k_prec_axis_reg(PrecAxisRegArgs<R> a) {
+  PrecAxisRegOp<R, L, NT, MODE>::template run<false>(hw_ctx(), a);
+}
+template <typename R, int L, int NT> __global__ void __launch_bounds__(NT) k_prec_rows_fwd_reg(PrecRowsRegArgs<R> a) {
+  PrecRowsFwdRegOp<R, L, NT>::template run<false>(hw_ctx(), a);
+}
+template <typename R, int L, int NT> __global__ void __launch_bounds__(NT) k_prec_rows_inv_reg(PrecRowsRegArgs<R> a) {
+  PrecRowsInvRegOp<R, L, NT>::template run<false>(hw_ctx(), a);
 }
 
 template <typename R> constexpr int prec_nt() { return sizeof(R) == 4 ? 512 : 256; }
+
+template <typename R, int L, int NT>
+static cudaError_t launch_prec_axis_reg_LN(cplx<R>* spec, long long axis_stride, long long n_inner,
+                                           long long outer_stride, long long n_outer, const cplx<R>* twn, int mode,
+                                           const DivArgs& dv, const cplx<R>* lt, const cplx<R>* lx,
+                                           const cplx<R>* ly, cudaStream_t st) {
+  constexpr int CP = NT / (L / 16);
+  const long long total = n_outer * n_inner;
+  const long long grid = (total + CP - 1) / CP;
+  const size_t smem = (size_t)L * CP * sizeof(cplx<R>);
+  const PrecAxisRegArgs<R> a{spec, axis_stride, n_inner, outer_stride, n_outer, twn, dv, lt, lx, ly};
+  if (mode == 0)
+    return launch_op<PrecAxisRegOp<R, L, NT, 0>>(k_prec_axis_reg<R, L, NT, 0>, (unsigned)grid, NT, smem, st, a);
+  if (mode == 1)
+    return launch_op<PrecAxisRegOp<R, L, NT, 1>>(k_prec_axis_reg<R, L, NT, 1>, (unsigned)grid, NT, smem, st, a);
+  return launch_op<PrecAxisRegOp<R, L, NT, 2>>(k_prec_axis_reg<R, L, NT, 2>, (unsigned)grid, NT, smem, st, a);
+}
 
 template <typename R, int L>
 static cudaError_t launch_prec_axis_reg_L(cplx<R>* spec, long long axis_stride, long long n_inner,
                                           long long outer_stride, long long n_outer, const cplx<R>* twn, int mode,
                                           const DivArgs& dv, const cplx<R>* lt, const cplx<R>* lx, const cplx<R>* ly,
                                           cudaStream_t st) {
-  constexpr int NT = prec_nt<R>();
-  constexpr int CP = NT / (L / 16);
-  const long long total = n_outer * n_inner;
-  const long long grid = (total + CP - 1) / CP;
-  const size_t smem = (size_t)L * CP * sizeof(cplx<R>);
-  if (mode == 0)
-    k_prec_axis_reg<R, L, NT, 0><<<(unsigned)grid, NT, smem, st>>>(spec, axis_stride, n_inner, outer_stride, n_outer,
-                                                                   twn, dv, lt, lx, ly);
-  else if (mode == 1)
-    k_prec_axis_reg<R, L, NT, 1><<<(unsigned)grid, NT, smem, st>>>(spec, axis_stride, n_inner, outer_stride, n_outer,
-                                                                   twn, dv, lt, lx, ly);
-  else
-    k_prec_axis_reg<R, L, NT, 2><<<(unsigned)grid, NT, smem, st>>>(spec, axis_stride, n_inner, outer_stride, n_outer,
-                                                                   twn, dv, lt, lx, ly);
-  note_launches(1);
-  return cudaGetLastError();
+  // a recorded (float) solve runs every launch with the executor's block size
+  if constexpr (prec_nt<R>() != kPersistThreads) {
+    if (recording())
+      return launch_prec_axis_reg_LN<R, L, kPersistThreads>(spec, axis_stride, n_inner, outer_stride, n_outer, twn,
+                                                            mode, dv, lt, lx, ly, st);
+  }
+  return launch_prec_axis_reg_LN<R, L, prec_nt<R>()>(spec, axis_stride, n_inner, outer_stride, n_outer, twn, mode, dv,
+                                                     lt, lx, ly, st);
 }
 
 #define FDE_FOR_EACH_PL(M) M(16) M(32) M(64) M(128) M(256) M(512) M(1024) M(2048) M(4096)
@@ -339,93 +284,23 @@ cudaError_t precond_reg_set_smem_attrs() {
 namespace fde {
 
 template <typename R, int L, int NT>
-__global__ void __launch_bounds__(NT) k_prec_rows_fwd_reg(const R* __restrict__ r, cplx<R>* __restrict__ spec,
-                                                           long long nrows, int H, int Hp,
-                                                           const cplx<R>* __restrict__ twn, Gate gate) {
-  if (gate_closed(gate)) return;
-  using C = cplx<R>;
-  constexpr int T = L / 16, PAIRS = NT / T, LS = L + L / 16;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  const int pr = threadIdx.x / T, t = threadIdx.x - pr * T;
-  const long long ra = ((long long)blockIdx.x * PAIRS + pr) * 2, rb = ra + 1;
-  C* my = sm + pr * LS;
-  auto at = [my](int, int pos) -> C& { return my[pos + (pos >> 4)]; };
-  const PadLayout<C, LS> lay{my};
-  C v[1][16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int p = t + q * T;
-    v[0][q] = mk<C>(ra < nrows ? r[ra * L + p] : (R)0, rb < nrows ? r[rb * L + p] : (R)0);
-  }
-  rf_forward<R, L, 1>(v, t, twn, lay);
-#pragma unroll
-  for (int idx = 0; idx < 16; ++idx) at(0, rf_freq<L>(t, idx)) = v[0][idx];
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int k = t + q * T;
-    if (k < H) {
-      const C zk = at(0, k);
-      const C zm = cconj(at(0, k == 0 ? 0 : L - k));
-      const C A = mk<C>((zk.x + zm.x) * (R)0.5, (zk.y + zm.y) * (R)0.5);
-      const C B = mk<C>((zk.y - zm.y) * (R)0.5, -(zk.x - zm.x) * (R)0.5);
-      if (ra < nrows) spec[ra * Hp + k] = A;
-      if (rb < nrows) spec[rb * Hp + k] = B;
-    }
-  }
-}
-
-template <typename R, int L, int NT>
-__global__ void __launch_bounds__(NT) k_prec_rows_inv_reg(const cplx<R>* __restrict__ spec, R* __restrict__ z,
-                                                           long long nrows, int H, int Hp,
-                                                           const cplx<R>* __restrict__ twn, Gate gate) {
-  if (gate_closed(gate)) return;
-  using C = cplx<R>;
-  constexpr int T = L / 16, PAIRS = NT / T, LS = L + L / 16;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  const int pr = threadIdx.x / T, t = threadIdx.x - pr * T;
-  const long long ra = ((long long)blockIdx.x * PAIRS + pr) * 2, rb = ra + 1;
-  C* my = sm + pr * LS;
-  const PadLayout<C, LS> lay{my};
-  C v[1][16];
-#pragma unroll
-  for (int idx = 0; idx < 16; ++idx) {
-    const int k = rf_freq<L>(t, idx);
-    const bool lo = k < H;
-    const int kk = lo ? k : L - k;
-    C A = ra < nrows ? spec[ra * Hp + kk] : mk<C>(0, 0);
-    C B = rb < nrows ? spec[rb * Hp + kk] : mk<C>(0, 0);
-    if (!lo) {
-      A = cconj(A);
-      B = cconj(B);
-    }
-    v[0][idx] = mk<C>(A.x - B.y, A.y + B.x);  // A + i B
-  }
-  rf_inverse<R, L, 1>(v, t, twn, lay);
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int p = t + q * T;
-    if (ra < nrows) z[ra * L + p] = v[0][q].x;
-    if (rb < nrows) z[rb * L + p] = v[0][q].y;
-  }
+static cudaError_t launch_prec_rows_reg_LN(int inverse, const R* r, R* z, cplx<R>* spec, long long nrows, int H,
+                                           int Hp, const cplx<R>* twn, cudaStream_t st, Gate gate) {
+  constexpr int PAIRS = NT / (L / 16);
+  const long long npairs = (nrows + 1) / 2;
+  const long long grid = (npairs + PAIRS - 1) / PAIRS;
+  const size_t smem = (size_t)PAIRS * (L + L / 16) * sizeof(cplx<R>);
+  const PrecRowsRegArgs<R> a{r, z, spec, nrows, H, Hp, twn, gate};
+  if (inverse)
+    return launch_op<PrecRowsInvRegOp<R, L, NT>>(k_prec_rows_inv_reg<R, L, NT>, (unsigned)grid, NT, smem, st, a);
+  return launch_op<PrecRowsFwdRegOp<R, L, NT>>(k_prec_rows_fwd_reg<R, L, NT>, (unsigned)grid, NT, smem, st, a);
 }
 
 template <typename R, int L>
 static cudaError_t launch_prec_rows_reg_L(int inverse, const R* r, R* z, cplx<R>* spec, long long nrows, int H,
                                           int Hp, const cplx<R>* twn, cudaStream_t st, Gate gate) {
-  constexpr int NT = 256;
-  constexpr int PAIRS = NT / (L / 16);
-  const long long npairs = (nrows + 1) / 2;
-  const long long grid = (npairs + PAIRS - 1) / PAIRS;
-  const size_t smem = (size_t)PAIRS * (L + L / 16) * sizeof(cplx<R>);
-  if (inverse)
-    k_prec_rows_inv_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(spec, z, nrows, H, Hp, twn, gate);
-  else
-    k_prec_rows_fwd_reg<R, L, NT><<<(unsigned)grid, NT, smem, st>>>(r, spec, nrows, H, Hp, twn, gate);
-  note_launches(1);
-  return cudaGetLastError();
+  static_assert(kPersistThreads == 256, "a recorded solve runs the rows transforms with the executor's block size");
+  return launch_prec_rows_reg_LN<R, L, 256>(inverse, r, z, spec, nrows, H, Hp, twn, st, gate);
 }
 
 template <typename R>

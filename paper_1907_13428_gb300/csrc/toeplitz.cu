@@ -61,8 +61,10 @@ static cudaError_t launch_rows(fde_problem* P, const R* x, int conj_sym, const c
   const Axis& A = P->ax[2];
   const AxisTables<R>& T = tables<R>(A);
   const int L = A.L;
-  const bool rec = recording();
-  if (L >= 16 && !rec) return launch_rows_reg<R, R>(P, x, conj_sym, sym ? sym : T.sym, T, E, st);
+  // a recorded solve: float passes register-resident (the executor's block
+  // size), double ones generic (bound by the double pipe either way)
+  const bool rec = recording(), gen = rec && sizeof(R) != 4;
+  if (L >= 16 && !gen) return launch_rows_reg<R, R>(P, x, conj_sym, sym ? sym : T.sym, T, E, st);
   const int threads = rec ? kPersistThreads : rows_threads<R>(L);
   const int cap = kEPT * threads;  // complex elements per CTA
   int pairs = cap / (2 * L);
@@ -82,16 +84,17 @@ static cudaError_t launch_axis(fde_problem* P, int axis, const R* x, int conj_sy
   const Axis& A = P->ax[axis];
   const AxisTables<R>& T = tables<R>(A);
   const int L = A.L;
-  const bool rec = recording();
+  const bool rec = recording(), gen = rec && sizeof(R) != 4;
   const int threads = rec ? kPersistThreads : (sizeof(R) == 4 ? 1024 : 512);
   const int cap = kEPT * threads;
   int pairs = cap / (2 * L);
   if (pairs < 1) pairs = 1;
   long long axis_stride, n_inner, outer_stride, n_outer;
   axis_geometry(P, axis, &axis_stride, &n_inner, &outer_stride, &n_outer);
-  if (L >= 16 && !rec)
+  if (L >= 16 && !gen)
     return launch_axis_reg<R, R>(L, x, A.n, axis_stride, n_inner, outer_stride, n_outer, sym ? sym : T.sym, T,
-                                 conj_sym, E, sizeof(R) == 4 ? P->axis_nt32 : P->axis_nt64, st);
+                                 conj_sym, E, rec ? kPersistThreads : sizeof(R) == 4 ? P->axis_nt32 : P->axis_nt64,
+                                 st);
   const long long total = n_outer * ((n_inner + 1) / 2);
   if (pairs > total) pairs = (int)total;
   const long long grid = (total + pairs - 1) / pairs;

@@ -63,20 +63,20 @@ template <typename R> struct EpiIn {
   R acc, x0, xn, add;
 };
 
-template <typename R>
+template <bool PS = false, typename R>
 __device__ __forceinline__ EpiIn<R> epi_load(const AxisEpi<R>& E, long long idx, int t) {
   EpiIn<R> in{0, 0, 0, 0};
   if (E.plain) return in;
-  if (E.acc) in.acc = E.acc[idx];
+  if (E.acc) in.acc = ldv<PS>(E.acc + idx);
   if (E.xt) {
-    if (!E.nb_only) in.x0 = E.xt[idx];
+    if (!E.nb_only) in.x0 = ldv<PS>(E.xt + idx);
     if (E.tdir > 0) {
-      if (t > 0) in.xn = E.xt[idx - E.plane];
+      if (t > 0) in.xn = ldv<PS>(E.xt + idx - E.plane);
     } else {
-      if (t < E.nt - 1) in.xn = E.xt[idx + E.plane];
+      if (t < E.nt - 1) in.xn = ldv<PS>(E.xt + idx + E.plane);
     }
   }
-  if (E.addv) in.add = E.addv[idx];
+  if (E.addv) in.add = ldv<PS>(E.addv + idx);
   return in;
 }
 

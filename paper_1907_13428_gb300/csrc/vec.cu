@@ -14,13 +14,15 @@ int red_grid(long long n) {
   return (int)g;
 }
 
+// The reduction kernels run with kRedThreads threads; their bounds admit the
+// executor's block size, with which recorded launches are replayed one by one.
 template <typename RA, typename RB>
-__global__ void __launch_bounds__(kRedThreads) k_dot(DotArgs<RA, RB> a) {
+__global__ void __launch_bounds__(kPersistThreads) k_dot(DotArgs<RA, RB> a) {
   DotOp<RA, RB>::template run<false>(hw_ctx(), a);
 }
 __global__ void __launch_bounds__(1024) k_finish(FinishArgs a) { FinishSumOp::run<false>(hw_ctx(), a); }
 template <typename RV>
-__global__ void __launch_bounds__(kRedThreads) k_pcg_xr(PcgXrArgs<RV> a) {
+__global__ void __launch_bounds__(kPersistThreads) k_pcg_xr(PcgXrArgs<RV> a) {
   PcgXrOp<RV>::template run<false>(hw_ctx(), a);
 }
 template <typename RV> __global__ void k_pcg_p(PcgPArgs<RV> a) { PcgPOp<RV>::template run<false>(hw_ctx(), a); }
@@ -31,7 +33,9 @@ __global__ void k_scalar_step(ScalarStepArgs a) { ScalarStepOp::run<false>(hw_ct
 template <typename R> __global__ void k_fill(FillArgs<R> a) { FillOp<R>::template run<false>(hw_ctx(), a); }
 template <typename R> __global__ void k_copy(CopyArgs<R> a) { CopyOp<R>::template run<false>(hw_ctx(), a); }
 __global__ void k_admm_pre(AdmmPreArgs a) { AdmmPreOp::run<false>(hw_ctx(), a); }
-__global__ void __launch_bounds__(kRedThreads) k_admm_post(AdmmPostArgs a) { AdmmPostOp::run<false>(hw_ctx(), a); }
+__global__ void __launch_bounds__(kPersistThreads) k_admm_post(AdmmPostArgs a) {
+  AdmmPostOp::run<false>(hw_ctx(), a);
+}
 __global__ void __launch_bounds__(1024) k_admm_finish(AdmmFinishArgs a) { AdmmFinishOp::run<false>(hw_ctx(), a); }
 __global__ void k_fold(FoldArgs a) { FoldOp::run<false>(hw_ctx(), a); }
 
@@ -78,15 +82,17 @@ static unsigned sgrid(long long n) {
   return (unsigned)g;
 }
 
-// one-block finishing kernels run with 1024 threads, and with the executor's
-// block size while launches are recorded (their bodies take any block size)
-static int fin_threads() { return recording() ? kPersistThreads : 1024; }
+// Block size of a launch: while launches are recorded, the executor's (every
+// body here takes any block size; the grids stay those of the plain launches).
+static int vthreads(int t) { return recording() ? kPersistThreads : t; }
+// one-block finishing kernels run with 1024 threads
+static int fin_threads() { return vthreads(1024); }
 
 template <typename RA, typename RB>
 cudaError_t dot(fde_problem* P, const RA* a, const RB* b, long long n, int slot, int op, cudaStream_t st,
                 double aux) {
   const int g = red_grid(n);
-  cudaError_t e = launch_op<DotOp<RA, RB>>(k_dot<RA, RB>, g, kRedThreads, 0, st, {a, b, n, P->partials});
+  cudaError_t e = launch_op<DotOp<RA, RB>>(k_dot<RA, RB>, g, vthreads(kRedThreads), 0, st, {a, b, n, P->partials});
   if (e != cudaSuccess) return e;
   return launch_op<FinishSumOp>(k_finish, 1, fin_threads(), 0, st, {P->partials, g, P->dscal, slot, op, aux});
 }
@@ -98,7 +104,7 @@ template cudaError_t dot<float, float>(fde_problem*, const float*, const float*,
 template <typename RV>
 cudaError_t pcg_xr(fde_problem* P, RV* x, RV* r, const RV* d, const RV* q, long long n, cudaStream_t st) {
   const int g = red_grid(n);
-  cudaError_t e = launch_op<PcgXrOp<RV>>(k_pcg_xr<RV>, g, kRedThreads, 0, st, {x, r, d, q, P->dscal, n, P->partials});
+  cudaError_t e = launch_op<PcgXrOp<RV>>(k_pcg_xr<RV>, g, vthreads(kRedThreads), 0, st, {x, r, d, q, P->dscal, n, P->partials});
   if (e != cudaSuccess) return e;
   return launch_op<FinishSumOp>(k_finish, 1, fin_threads(), 0, st, {P->partials, g, P->dscal, S_RR, FIN_STORE, 0.0});
 }
@@ -108,7 +114,7 @@ template cudaError_t pcg_xr<float>(fde_problem*, float*, float*, const float*, c
 
 template <typename RV>
 cudaError_t pcg_p(fde_problem* P, RV* d, const RV* z, long long n, cudaStream_t st) {
-  return launch_op<PcgPOp<RV>>(k_pcg_p<RV>, sgrid(n), 256, 0, st, {d, z, P->dscal, n});
+  return launch_op<PcgPOp<RV>>(k_pcg_p<RV>, sgrid(n), vthreads(256), 0, st, {d, z, P->dscal, n});
 }
 template cudaError_t pcg_p<double>(fde_problem*, double*, const double*, long long, cudaStream_t);
 template cudaError_t pcg_p<float>(fde_problem*, float*, const float*, long long, cudaStream_t);
@@ -124,19 +130,19 @@ cudaError_t residual(fde_problem* P, const double* b, const double* s, double* r
 }
 
 cudaError_t to_f32(const double* in, float* out, long long n, cudaStream_t st) {
-  return launch_op<ToF32Op>(k_to_f32, sgrid(n), 256, 0, st, {in, out, n});
+  return launch_op<ToF32Op>(k_to_f32, sgrid(n), vthreads(256), 0, st, {in, out, n});
 }
 cudaError_t to_f32_unless_conv(fde_problem* P, const double* in, float* out, long long n, cudaStream_t st) {
-  return launch_op<ToF32UnlessOp>(k_to_f32_unless, sgrid(n), 256, 0, st, {in, out, n, P->dscal});
+  return launch_op<ToF32UnlessOp>(k_to_f32_unless, sgrid(n), vthreads(256), 0, st, {in, out, n, P->dscal});
 }
 cudaError_t add_f32_unless_conv(fde_problem* P, double* y, const float* d, long long n, cudaStream_t st) {
-  cudaError_t e = launch_op<ScalarStepOp>(k_scalar_step, 1, recording() ? kPersistThreads : 1, 0, st,
+  cudaError_t e = launch_op<ScalarStepOp>(k_scalar_step, 1, vthreads(1), 0, st,
                                           {P->dscal, 0, 0, 1});
   if (e != cudaSuccess) return e;
-  return launch_op<AddF32UnlessOp>(k_add_f32_unless, sgrid(n), 256, 0, st, {y, d, n, P->dscal});
+  return launch_op<AddF32UnlessOp>(k_add_f32_unless, sgrid(n), vthreads(256), 0, st, {y, d, n, P->dscal});
 }
 cudaError_t scalar_max(fde_problem* P, int dst, int src, cudaStream_t st) {
-  return launch_op<ScalarStepOp>(k_scalar_step, 1, recording() ? kPersistThreads : 1, 0, st, {P->dscal, dst, src, 0});
+  return launch_op<ScalarStepOp>(k_scalar_step, 1, vthreads(1), 0, st, {P->dscal, dst, src, 0});
 }
 cudaError_t add_f32(double* y, const float* d, long long n, cudaStream_t st) {
   k_add_f32<<<sgrid(n), 256, 0, st>>>(y, d, n);
@@ -145,33 +151,33 @@ cudaError_t add_f32(double* y, const float* d, long long n, cudaStream_t st) {
 }
 template <typename R>
 cudaError_t fill(R* x, R v, long long n, cudaStream_t st) {
-  return launch_op<FillOp<R>>(k_fill<R>, sgrid(n), 256, 0, st, {x, v, n});
+  return launch_op<FillOp<R>>(k_fill<R>, sgrid(n), vthreads(256), 0, st, {x, v, n});
 }
 template cudaError_t fill<double>(double*, double, long long, cudaStream_t);
 template cudaError_t fill<float>(float*, float, long long, cudaStream_t);
 template <typename R>
 cudaError_t copy(R* dst, const R* src, long long n, cudaStream_t st) {
-  return launch_op<CopyOp<R>>(k_copy<R>, sgrid(n), 256, 0, st, {dst, src, n});
+  return launch_op<CopyOp<R>>(k_copy<R>, sgrid(n), vthreads(256), 0, st, {dst, src, n});
 }
 template cudaError_t copy<double>(double*, const double*, long long, cudaStream_t);
 template cudaError_t copy<float>(float*, const float*, long long, cudaStream_t);
 
 cudaError_t admm_pre(const AdmmArgs& A, double* c, double* bu, double* r0, double* q, cudaStream_t st) {
-  return launch_op<AdmmPreOp>(k_admm_pre, sgrid(A.n), 256, 0, st, {A, c, bu, r0, q});
+  return launch_op<AdmmPreOp>(k_admm_pre, sgrid(A.n), vthreads(256), 0, st, {A, c, bu, r0, q});
 }
 
 cudaError_t admm_post(fde_problem* P, const AdmmArgs& A, const double* y, const double* By, const double* bu,
                       const double* r0, double* u, cudaStream_t st) {
   int g = red_grid(A.n);
   if (g > kMaxPartials / 5) g = kMaxPartials / 5;
-  cudaError_t e = launch_op<AdmmPostOp>(k_admm_post, g, kRedThreads, 0, st, {A, y, By, bu, r0, u, P->partials, g});
+  cudaError_t e = launch_op<AdmmPostOp>(k_admm_post, g, vthreads(kRedThreads), 0, st, {A, y, By, bu, r0, u, P->partials, g});
   if (e != cudaSuccess) return e;
   return launch_op<AdmmFinishOp>(k_admm_finish, 1, fin_threads(), 0, st, {P->partials, g, P->dscal});
 }
 
 cudaError_t fold(const double* t, const double* q, const double* c, const double* y, const double m2inv[2],
                  const double m1[2], long long last_start, long long n, double* v, double* w, cudaStream_t st) {
-  return launch_op<FoldOp>(k_fold, sgrid(n), 256, 0, st,
+  return launch_op<FoldOp>(k_fold, sgrid(n), vthreads(256), 0, st,
                            {t, q, c, y, m2inv[0], m2inv[1], m1[0], m1[1], last_start, n, v, w});
 }
 

@@ -5,9 +5,10 @@ The executor replays the launches the batch solve records, so its reference is
 the same launches issued one by one (replay=True): the results must agree bit
 for bit, whatever the split of the CTAs into instance groups. The results are
 also checked against the oracle's ADMM after K iterations (1e-8, every
-sub-problem solved tightly on both sides), and the bounded waits are exercised:
-a group whose first CTA never arrives at its barrier ends the kernel with
-FDE_ETIMEOUT, and the context stays usable for the next solve."""
+sub-problem solved tightly on both sides), and the bounded waits are exercised
+in both schedules (lockstep, instance groups): a CTA that never arrives at its
+barrier ends the kernel with FDE_ETIMEOUT, and the context stays usable for the
+next solve."""
 import numpy as np
 import pytest
 import torch
@@ -45,12 +46,13 @@ def test_persistent_equals_stream_replay_bitwise():
     fo = F.AdmmOptions(delta=1.0, rho=1.618, max_admm=3, inner_tol=1e-10, precision=F.FDE_MIXED,
                        inner_tol_mixed=1e-5, max_refine=3, max_pcg=20)
     yr, ur, sr, _, _ = _solve(b, fo, insts, replay=True)
-    for gc in (0, 1, 7, 100000):  # default split, one CTA per group, 7 CTAs, one group of all CTAs
-        yp, up, sp, info, st = _solve(b, fo, insts, group_ctas=gc)
+    # lockstep; instance groups: default split, one CTA per group, 7 CTAs, one group of all CTAs
+    for sched, gc in ((0, 0), (1, 0), (1, 1), (1, 7), (1, 100000)):
+        yp, up, sp, info, st = _solve(b, fo, insts, group_ctas=gc, schedule=sched)
         assert st == F.FDE_OK
-        assert info["groups"] >= 1 and info["commands"] > 0
+        assert info["schedule"] == sched and info["groups"] >= 1 and info["commands"] > 0
         for a, c in zip(yr + ur, yp + up):
-            assert np.array_equal(a, c), gc
+            assert np.array_equal(a, c), (sched, gc)
         for a, c in zip(sr, sp):
             assert a["pcg_iters"] == c["pcg_iters"] and a["max_sub_relres"] == c["max_sub_relres"]
     b.close()
@@ -85,16 +87,22 @@ def test_persistent_bounded_wait_returns_timeout():
     b = F.Batch([i.params for i in insts])
     fo = F.AdmmOptions(delta=1.0, rho=1.618, max_admm=2, inner_tol=1e-10, precision=F.FDE_MIXED,
                        inner_tol_mixed=1e-5, max_refine=2, max_pcg=10)
-    # group 0's first CTA never arrives: every wait of group 0 runs out after 50 ms
-    _, _, _, info, st = _solve(b, fo, insts, group_ctas=4, timeout_s=0.05, stall_group=1, check=False)
+    yr, _, _, _, _ = _solve(b, fo, insts, replay=True)
+    # instance groups: group 0's first CTA never arrives at the barrier after its
+    # claim, so every wait of group 0 runs out after 50 ms
+    _, _, _, info, st = _solve(b, fo, insts, group_ctas=4, schedule=1, timeout_s=0.05, stall_group=1, check=False)
     assert st == F.FDE_ETIMEOUT
     assert info["timeout_group"] == 0 and info["timeout_command"] == -1
-    # the context is usable: the next solve runs and equals the reference executor
-    yp, _, _, _, st = _solve(b, fo, insts, group_ctas=4)
-    assert st == F.FDE_OK
-    yr, _, _, _, _ = _solve(b, fo, insts, replay=True)
-    for a, c in zip(yp, yr):
-        assert np.array_equal(a, c)
+    # lockstep: the first CTA runs step 0 and never arrives at its barrier
+    _, _, _, info, st = _solve(b, fo, insts, timeout_s=0.05, stall_group=1, check=False)
+    assert st == F.FDE_ETIMEOUT
+    assert info["schedule"] == 0 and info["timeout_group"] == 0 and info["timeout_command"] == 0
+    # the context is usable: the next solves run and equal the reference executor
+    for sched in (0, 1):
+        yp, _, _, _, st = _solve(b, fo, insts, group_ctas=4, schedule=sched)
+        assert st == F.FDE_OK
+        for a, c in zip(yp, yr):
+            assert np.array_equal(a, c)
     torch.cuda.synchronize()
     b.close()
 
@@ -136,6 +144,7 @@ def test_persistent_batch_workload_64_uneven_instances():
     for s, y, u in zip(stats, ys, us):
         assert s["max_sub_relres"] <= 1e-8, s
         assert torch.isfinite(y).all() and torch.isfinite(u).all()
+    assert info["schedule"] == 0  # the fixed budgets make every instance's launch sequence alike
     ys, _, _, _, _ = b.admm_solve_persistent(fo, ybars, replay=True, **kw)
     for a, y in zip(yp, ys):
         assert np.array_equal(a, host(y))
