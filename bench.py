@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "medium", "small", "slab", "batch", "paper-table5"])
+    ap.add_argument("--workload", default="large", choices=["large", "medium", "small", "slab", "batch", "paper-table5",
+                                                              "paper-table6"])
     ap.add_argument("--admm-iters", type=int, default=20)
     ap.add_argument("--sub-tol", type=float, default=1e-8)
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 comparison, e2e and CPU baseline")
@@ -828,60 +829,99 @@ PAPER_TABLE5 = [(8, 2.0, 0.387, 5.23e-4, 12, 86, 1.89), (16, 2.0, 0.502, 8.68e-5
                 (100, 0.1, 0.670, 4.91e-3, 17, 119, 2436.17), (128, 0.1, 0.673, 3.49e-3, 17, 169, 9077.08)]
 
 
-def run_paper_table5(args):
-    """The grid sweep of Table 5 in the paper's own setting (Section 6.1: n^3 grid,
-    h_t = h_x, Riesz beta = 1.3, time order 0.7, the analytic desired state, symmetric
-    boxes y in [-4, 4], u in [-350, 350], rho = 1.618, ADMM tolerance 1e-4, the inner
-    rule 0.05 max{min residuals, 1e-4}), solved on the GPU in FP64 with every PCG
-    started from zero (MATLAB pcg's default initial guess), in FP64 with PCG started
-    from the previous iterate, and in mixed precision. Per row: ADMM iterations, average PCG iterations per ADMM iteration,
-    the misfit E_L2, the dual infeasibility and the solve time, beside the paper's
-    printed row (context: its numbers come from MATLAB's pcg on a 6-core CPU)."""
+# Table 6 of the paper (box constraints on both variables, varying fractional orders;
+# y_a = -4, u_a = -350, gamma = 1e-4): time order alpha, space order beta, delta, misfit,
+# dual infeasibility, average PCG iterations, ADMM iterations, MATLAB time in seconds. The
+# caption's grid reads 32^4; its misfits and times match the 50^3 rows of the grid sweep,
+# so it is run at 50^3.
+PAPER_TABLE6 = [(0.1, 1.3, 0.4, 0.646, 1.60e-4, 17, 126, 380.75), (0.3, 1.3, 0.4, 0.646, 2.56e-4, 17, 126, 385.96),
+                (0.5, 1.3, 0.4, 0.512, 2.83e-4, 18, 126, 408.47), (0.9, 1.3, 0.4, 0.644, 3.10e-4, 19, 125, 419.46),
+                (0.7, 1.1, 0.4, 0.648, 1.21e-3, 30, 100, 508.59), (0.7, 1.5, 0.1, 0.779, 4.23e-4, 15, 96, 275.03),
+                (0.7, 1.7, 0.4, 1.04, 2.46e-4, 13, 113, 275.21), (0.7, 1.9, 0.1, 1.36, 1.36e-3, 8, 108, 180.85)]
+
+
+def _paper_solves(F, dev, n, alpha, beta, delta, modes):
+    """One row of the paper's experiments in its own setting (Section 6.1: n^3 grid,
+    h_t = h_x, Riesz coefficients of order beta in both space directions, time order
+    alpha, the analytic desired state, boxes y in [-4, 4], u in [-350, 350],
+    rho = 1.618, ADMM tolerance 1e-4, the inner rule 0.05 max{min residuals, 1e-4}),
+    solved on the GPU in each of `modes` (name, precision, inner_x0). Per mode: ADMM
+    iterations, average PCG iterations per ADMM iteration, the misfit E_L2, the dual
+    infeasibility and the solve time."""
     import torch
     import fde_inputs as fi
+    c = -1.0 / (2.0 * math.cos(beta * math.pi / 2.0))
+    p = fi.FdeParams(nx=n, ny=n, nt=n, T=1.0, beta_x=beta, beta_y=beta, alpha_t=alpha, dp=c, dm=c, ep=c, em=c,
+                     gamma=1e-4, weights=0, time_step_mode=1)
+    ybar_np = fi.desired_state_paper(p)
+    prob = F.Problem(p)
+    ybar = torch.as_tensor(ybar_np.ravel(), device=dev)
+    bounds = dict(ya=-4.0, yb=4.0, ua=-350.0, ub=350.0)
+    out = {}
+    for name, prec, x0 in modes:
+        o = F.AdmmOptions(delta=delta, rho=1.618, tol_admm=1e-4, max_admm=5000, inner_tol_mode=0,
+                          precision=prec, max_pcg=2000, inner_x0=x0)
+        prob.admm_solve(o, ybar, **bounds, allow_noconv=True)  # warm-up (tables, first-use allocations)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = prob.admm_solve(o, ybar, **bounds, allow_noconv=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        s = r["stats"]
+        it = prob.iterates()
+        hx = 1.0 / (n + 1)
+        w = torch.ones(n, n, n, dtype=torch.float64, device=dev)
+        w[-1] = 0.5
+        w = w.view(-1)
+        d = it["y"] - ybar
+        misfit = math.sqrt(hx ** 3 * float(torch.sum(w * d * d)))
+        btp = prob.matvec(it["p"], F.FDE_OP_BT)
+        psi = prob.psi
+        dual_y = float((w * d + btp + it["wy"]).abs().max())
+        dual_u = float((1e-4 * w * it["u"] + psi * it["p"] + psi * it["wu"]).abs().max())
+        out[name] = {"status": r["status"], "admm": s["admm_iters"],
+                     "pcg_avg": s["pcg_iters"] / max(1, s["admm_iters"]), "E_L2": misfit,
+                     "dual_inf": max(dual_y, dual_u), "time_s": dt,
+                     "residuals": [s["res_eq"], s["res_y"], s["res_u"]]}
+    prob.close()
+    return out
+
+
+def run_paper_table5(args):
+    """The grid sweep of Table 5 (beta = 1.3, time order 0.7, n = 8..128), solved in
+    FP64 with every PCG started from zero (MATLAB pcg's default initial guess), in FP64
+    with PCG started from the previous iterate, and in mixed precision, beside the
+    paper's printed rows (context: its numbers come from MATLAB's pcg on a 6-core CPU)."""
+    import torch
     import paper_1907_13428_gb300 as F
     dev = torch.device("cuda", 0)
+    modes = (("fp64_pcg_from_zero", F.FDE_FP64, 1), ("fp64", F.FDE_FP64, 0), ("mixed_dfv", F.FDE_MIXED_DFV, 0))
     rows = []
     for n, delta, e_p, dinf_p, pcg_p, admm_p, t_p in PAPER_TABLE5:
-        c = -1.0 / (2.0 * math.cos(1.3 * math.pi / 2.0))
-        p = fi.FdeParams(nx=n, ny=n, nt=n, T=1.0, beta_x=1.3, beta_y=1.3, alpha_t=0.7, dp=c, dm=c, ep=c, em=c,
-                         gamma=1e-4, weights=0, time_step_mode=1)
-        ybar_np = fi.desired_state_paper(p)
-        prob = F.Problem(p)
-        ybar = torch.as_tensor(ybar_np.ravel(), device=dev)
-        bounds = dict(ya=-4.0, yb=4.0, ua=-350.0, ub=350.0)
-        row = {"n": n, "N": p.N, "delta": delta,
+        row = {"n": n, "N": n ** 3, "delta": delta,
                "paper": {"E_L2": e_p, "dual_inf": dinf_p, "pcg_avg": pcg_p, "admm": admm_p, "time_s": t_p}}
-        for name, prec, x0 in (("fp64_pcg_from_zero", F.FDE_FP64, 1), ("fp64", F.FDE_FP64, 0),
-                               ("mixed_dfv", F.FDE_MIXED_DFV, 0)):
-            o = F.AdmmOptions(delta=delta, rho=1.618, tol_admm=1e-4, max_admm=5000, inner_tol_mode=0,
-                              precision=prec, max_pcg=2000, inner_x0=x0)
-            prob.admm_solve(o, ybar, **bounds, allow_noconv=True)  # warm-up (tables, first-use allocations)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            r = prob.admm_solve(o, ybar, **bounds, allow_noconv=True)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            s = r["stats"]
-            it = prob.iterates()
-            hx = 1.0 / (n + 1)
-            w = torch.ones(n, n, n, dtype=torch.float64, device=dev)
-            w[-1] = 0.5
-            w = w.view(-1)
-            d = it["y"] - ybar
-            misfit = math.sqrt(hx ** 3 * float(torch.sum(w * d * d)))
-            btp = prob.matvec(it["p"], F.FDE_OP_BT)
-            psi = prob.psi
-            dual_y = float((w * d + btp + it["wy"]).abs().max())
-            dual_u = float((1e-4 * w * it["u"] + psi * it["p"] + psi * it["wu"]).abs().max())
-            row[name] = {"status": r["status"], "admm": s["admm_iters"],
-                         "pcg_avg": s["pcg_iters"] / max(1, s["admm_iters"]), "E_L2": misfit,
-                         "dual_inf": max(dual_y, dual_u), "time_s": dt,
-                         "residuals": [s["res_eq"], s["res_y"], s["res_u"]]}
-        prob.close()
+        row.update(_paper_solves(F, dev, n, 0.7, 1.3, delta, modes))
         rows.append(row)
         print(json.dumps(row), file=sys.stderr, flush=True)
     print(json.dumps({"workload": "paper Table 5 sweep", "rows": rows}), flush=True)
+
+
+def run_paper_table6(args):
+    """The fractional-order sweep of Table 6 at 50^3 (time order alpha, space order
+    beta, the paper's delta per row), solved in FP64 with every PCG started from zero
+    and in mixed precision, beside the paper's printed rows."""
+    import torch
+    import paper_1907_13428_gb300 as F
+    dev = torch.device("cuda", 0)
+    modes = (("fp64_pcg_from_zero", F.FDE_FP64, 1), ("mixed_dfv", F.FDE_MIXED_DFV, 0))
+    rows = []
+    for alpha, beta, delta, e_p, dinf_p, pcg_p, admm_p, t_p in PAPER_TABLE6:
+        row = {"alpha": alpha, "beta": beta, "n": 50, "delta": delta,
+               "paper": {"E_L2": e_p, "dual_inf": dinf_p, "pcg_avg": pcg_p, "admm": admm_p, "time_s": t_p}}
+        row.update(_paper_solves(F, dev, 50, alpha, beta, delta, modes))
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"workload": "paper Table 6 sweep", "rows": rows}), flush=True)
 
 
 def main():
@@ -894,6 +934,8 @@ def main():
         run_batch(args)
     elif args.workload == "paper-table5":
         run_paper_table5(args)
+    elif args.workload == "paper-table6":
+        run_paper_table6(args)
     else:
         run_ours(args)
 

@@ -4,8 +4,9 @@ coefficients (Eq. Riesz matrix), h_t = h_x, the Section 6.1 desired state and
 inner-tolerance rule.
 
 Parity: ADMM after K iterations against the oracle's exact sub-solves (FP64
-1e-10). Trend (Table 5): with the preconditioner the average PCG count per
-ADMM iteration stays roughly flat as the grid is refined."""
+1e-10). Trends: with the preconditioner the average PCG count per ADMM
+iteration stays roughly flat as the grid is refined (Table 5) and grows as the
+space order tends to 1 (Table 6)."""
 import math
 
 import numpy as np
@@ -57,6 +58,26 @@ def test_paper_mode_pcg_counts_flat_in_n():
         prob.close()
     assert max(avg) <= 3 * min(avg) + 5, avg
     assert max(avg) < 60, avg
+
+
+def test_paper_order_sweep_pcg_slower_as_beta_tends_to_one():
+    """Table 6 trend: with the space order beta close to 1 the preconditioned
+    normal equations are harder (the paper: 30 PCG iterations per ADMM iteration
+    at beta = 1.1 against 13-19 at beta = 1.3-1.7). Every PCG started from zero
+    (MATLAB pcg's default), Section 6.1 inner rule, n = 32, delta = 0.4."""
+    need_gpu()
+    F = lib()
+    avg = {}
+    for beta in (1.1, 1.7):
+        inst = paper_instance(32, beta=beta)
+        prob = F.Problem(inst.params)
+        fo = F.AdmmOptions(delta=0.4, rho=1.618, tol_admm=1e-4, max_admm=3000, inner_tol_mode=0, inner_x0=1)
+        r = prob.admm_solve(fo, dev(inst.ybar), ya=inst.ya, yb=inst.yb, ua=inst.ua, ub=inst.ub, allow_noconv=True)
+        s = r["stats"]
+        assert r["status"] == F.FDE_OK, s
+        avg[beta] = s["pcg_iters"] / max(1, s["admm_iters"])
+        prob.close()
+    assert avg[1.1] > 1.5 * avg[1.7], avg
 
 
 def test_paper_50_cubed_interior_solution_and_misfit():
