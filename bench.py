@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=["large", "medium", "small", "slab", "batch", "paper-table5",
-                                                              "paper-table6"])
+                                                              "paper-table6", "paper-tables-50"])
     ap.add_argument("--admm-iters", type=int, default=20)
     ap.add_argument("--sub-tol", type=float, default=1e-8)
     ap.add_argument("--no-extras", action="store_true", help="skip FP64 comparison, e2e and CPU baseline")
@@ -840,27 +840,32 @@ PAPER_TABLE6 = [(0.1, 1.3, 0.4, 0.646, 1.60e-4, 17, 126, 380.75), (0.3, 1.3, 0.4
                 (0.7, 1.7, 0.4, 1.04, 2.46e-4, 13, 113, 275.21), (0.7, 1.9, 0.1, 1.36, 1.36e-3, 8, 108, 180.85)]
 
 
-def _paper_solves(F, dev, n, alpha, beta, delta, modes):
+def _paper_solves(F, dev, n, alpha, beta, delta, modes, gamma=1e-4, ya=-4.0, ua=-350.0):
     """One row of the paper's experiments in its own setting (Section 6.1: n^3 grid,
     h_t = h_x, Riesz coefficients of order beta in both space directions, time order
-    alpha, the analytic desired state, boxes y in [-4, 4], u in [-350, 350],
-    rho = 1.618, ADMM tolerance 1e-4, the inner rule 0.05 max{min residuals, 1e-4}),
-    solved on the GPU in each of `modes` (name, precision, inner_x0). Per mode: ADMM
-    iterations, average PCG iterations per ADMM iteration, the misfit E_L2, the dual
-    infeasibility and the solve time."""
+    alpha, the analytic desired state, symmetric boxes y in [ya, -ya], u in [ua, -ua]
+    (None: unbounded), rho = 1.618, ADMM tolerance 1e-4, the inner rule
+    0.05 max{min residuals, 1e-4}), solved on the GPU in each of `modes` (name,
+    precision, inner_x0[, a fixed sub-solve tolerance instead of the inner rule]). Per
+    mode: ADMM iterations, average PCG iterations per ADMM iteration, the misfit E_L2,
+    the dual infeasibility and the solve time."""
     import torch
     import fde_inputs as fi
     c = -1.0 / (2.0 * math.cos(beta * math.pi / 2.0))
     p = fi.FdeParams(nx=n, ny=n, nt=n, T=1.0, beta_x=beta, beta_y=beta, alpha_t=alpha, dp=c, dm=c, ep=c, em=c,
-                     gamma=1e-4, weights=0, time_step_mode=1)
+                     gamma=gamma, weights=0, time_step_mode=1)
     ybar_np = fi.desired_state_paper(p)
     prob = F.Problem(p)
     ybar = torch.as_tensor(ybar_np.ravel(), device=dev)
-    bounds = dict(ya=-4.0, yb=4.0, ua=-350.0, ub=350.0)
+    bounds = {}
+    if ya is not None:
+        bounds.update(ya=float(ya), yb=-float(ya))
+    if ua is not None:
+        bounds.update(ua=float(ua), ub=-float(ua))
     out = {}
-    for name, prec, x0 in modes:
-        o = F.AdmmOptions(delta=delta, rho=1.618, tol_admm=1e-4, max_admm=5000, inner_tol_mode=0,
-                          precision=prec, max_pcg=2000, inner_x0=x0)
+    for name, prec, x0, *fixed in modes:
+        o = F.AdmmOptions(delta=delta, rho=1.618, tol_admm=1e-4, max_admm=5000, inner_tol_mode=1 if fixed else 0,
+                          inner_tol=fixed[0] if fixed else 1e-8, precision=prec, max_pcg=2000, inner_x0=x0)
         prob.admm_solve(o, ybar, **bounds, allow_noconv=True)  # warm-up (tables, first-use allocations)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -878,13 +883,57 @@ def _paper_solves(F, dev, n, alpha, beta, delta, modes):
         btp = prob.matvec(it["p"], F.FDE_OP_BT)
         psi = prob.psi
         dual_y = float((w * d + btp + it["wy"]).abs().max())
-        dual_u = float((1e-4 * w * it["u"] + psi * it["p"] + psi * it["wu"]).abs().max())
+        dual_u = float((gamma * w * it["u"] + psi * it["p"] + psi * it["wu"]).abs().max())
         out[name] = {"status": r["status"], "admm": s["admm_iters"],
                      "pcg_avg": s["pcg_iters"] / max(1, s["admm_iters"]), "E_L2": misfit,
                      "dual_inf": max(dual_y, dual_u), "time_s": dt,
                      "residuals": [s["res_eq"], s["res_y"], s["res_u"]]}
     prob.close()
     return out
+
+
+# Tables 2, 3, 4 and 7 of the paper at 50^3 (beta = 1.3, alpha = 0.7): table, gamma, y_a,
+# u_a (None: that variable unbounded), delta, misfit, dual infeasibility, average PCG
+# iterations, ADMM iterations, MATLAB time in seconds.
+PAPER_TABLES_50 = [
+    ("2", 1e-4, -7, None, 0.1, 0.560, 2.13e-3, 9, 75, 142.31),
+    ("2", 1e-4, -5, None, 0.1, 0.580, 3.14e-3, 10, 105, 206.73),
+    ("2", 1e-4, -3, None, 0.1, 0.788, 4.11e-3, 10, 100, 193.77),
+    ("2", 1e-4, -1, None, 0.1, 1.38, 8.74e-4, 10, 86, 173.49),
+    ("3", 1e-4, None, -400, 0.4, 0.560, 8.43e-4, 16, 30, 84.46),
+    ("3", 1e-4, None, -300, 0.4, 0.565, 8.79e-4, 19, 22, 72.77),
+    ("3", 1e-4, None, -200, 0.4, 0.625, 4.39e-4, 17, 28, 85.55),
+    ("3", 1e-4, None, -100, 0.4, 0.890, 1.49e-4, 18, 65, 205.69),
+    ("4", 1e-4, -7, -400, 0.4, 0.560, 4.88e-3, 10, 36, 74.20),
+    ("4", 1e-4, -7, -200, 0.4, 0.594, 2.35e-3, 11, 38, 80.14),
+    ("4", 1e-4, -4, -350, 0.4, 0.645, 1.99e-4, 18, 126, 412.66),
+    ("4", 1e-4, -1, -400, 0.4, 1.38, 2.56e-4, 19, 109, 377.86),
+    ("7", 1e-2, -2, -100, 0.1, 1.77, 1.38e-3, 11, 87, 190.99),
+    ("7", 1e-4, -7, -400, 0.4, 0.560, 4.88e-3, 10, 36, 74.20),
+    ("7", 1e-6, -9, -2800, 10.0, 0.128, 6.03e-4, 8, 47, 71.13),
+    ("7", 1e-8, -9, -4000, 100.0, 0.113, 2.18e-4, 6, 32, 44.70),
+    ("7", 1e-10, -9, -4000, 100.0, 0.113, 2.18e-4, 5, 32, 40.77)]
+
+
+def run_paper_tables_50(args):
+    """The bound and regularization sweeps of Tables 2 (state box), 3 (control box),
+    4 (both boxes) and 7 (gamma, with the bounds and delta of each row) at 50^3, solved
+    in FP64 with every PCG started from zero (the paper's inner rule) and in mixed
+    precision with sub-solves to a fixed 1e-8 (with the inner rule's 5e-6 floor the
+    mixed sub-solves can stall the ADMM on the control-box rows), beside the paper's
+    printed rows."""
+    import torch
+    import paper_1907_13428_gb300 as F
+    dev = torch.device("cuda", 0)
+    modes = (("fp64_pcg_from_zero", F.FDE_FP64, 1), ("mixed_dfv_fixed_1e-8", F.FDE_MIXED_DFV, 0, 1e-8))
+    rows = []
+    for table, gamma, ya, ua, delta, e_p, dinf_p, pcg_p, admm_p, t_p in PAPER_TABLES_50:
+        row = {"table": table, "gamma": gamma, "y_a": ya, "u_a": ua, "n": 50, "delta": delta,
+               "paper": {"E_L2": e_p, "dual_inf": dinf_p, "pcg_avg": pcg_p, "admm": admm_p, "time_s": t_p}}
+        row.update(_paper_solves(F, dev, 50, 0.7, 1.3, delta, modes, gamma=gamma, ya=ya, ua=ua))
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"workload": "paper Tables 2, 3, 4, 7 at 50^3", "rows": rows}), flush=True)
 
 
 def run_paper_table5(args):
@@ -936,6 +985,8 @@ def main():
         run_paper_table5(args)
     elif args.workload == "paper-table6":
         run_paper_table6(args)
+    elif args.workload == "paper-tables-50":
+        run_paper_tables_50(args)
     else:
         run_ours(args)
 
