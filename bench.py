@@ -415,6 +415,42 @@ def batch_extra(F, dev, admm_iters=5):
                               "(register-resident float transforms, generic double ones) with bounded barriers"}}
 
 
+def grad_extra(F, dev, admm_iters=50):
+    """The differentiation workload (256^2x64, beta = 1.5, control box [-1, 1]): an FP64
+    ADMM solve of a fixed number of iterations (sub-problems to 1e-10), then the
+    gradient of J* with respect to the desired state and the four diffusion
+    coefficients (fde_admm_grad: adjoint PCG on B B^T to 1e-12), each timed after a
+    warm-up call."""
+    import torch
+    import fde_inputs as fi
+    inst = fi.config_grad()
+    prob = F.Problem(inst.params)
+    ybar = torch.as_tensor(inst.ybar.ravel(), device=dev)
+    o = F.AdmmOptions(delta=1.0, rho=1.618, max_admm=admm_iters, fixed_iters=True, inner_tol_mode=1,
+                      inner_tol=1e-10, precision=F.FDE_FP64)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, out
+
+    t_solve, r = timed(lambda: prob.admm_solve(o, ybar, ua=inst.ua, ub=inst.ub, allow_noconv=True))
+    it = prob.iterates(("y", "wy"))
+    t_grad, (dJ, coef, pv) = timed(lambda: prob.admm_grad(it["y"], ybar, it["wy"], tol=1e-12))
+    res = {"workload": "256x256x64, beta 1.5, control box [-1, 1], gamma 1e-4; FP64 ADMM %d iterations "
+                       "(sub-problems to 1e-10), then dJ/dybar and dJ/d(d+, d-, e+, e-) by the adjoint "
+                       "(PCG on B B^T to 1e-12)" % admm_iters,
+           "solve_s": t_solve, "grad_s": t_grad, "pcg_iters": r["stats"]["pcg_iters"],
+           "dJ_dcoef": [float(c) for c in coef], "dJ_dybar_norm": float(torch.linalg.vector_norm(dJ))}
+    prob.close()
+    del ybar, dJ, pv
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -661,6 +697,7 @@ def run_ours(args):
         del y_ref, u_ref
         if not args.skip_variants:
             extras["batch_workload"] = batch_extra(F, dev)
+            extras["grad_workload"] = grad_extra(F, dev)
         if rank == 0:
             counts = oracle_operation_counts(inst, args.admm_iters, args.sub_tol)
             extras["cpu_baseline"] = cpu_baseline(inst, counts)
